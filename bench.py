@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput of the whole epsilon-graph method on one GB300.
+
+A step is one msm_eps_graph call over the 1,000,000 x 128 workload (sign
+projection to 128-bit strings, blockwise MSM with k = 10 blocks and d = 6
+over Q replicates, epsilon recheck), inputs resident in HBM.  Prints one
+JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "points/sec to full ε-graph at 1M×128 vs plain FP32, at equal missing-edge ratio"
+UNIT = "points/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--Q", type=int, default=11)
+    ap.add_argument("--n", type=int, default=0, help="override n (0 = workload's)")
+    ap.add_argument("--cpu-sample", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-missing", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(wl, n, Q):
+    return (f"scale: n={n:,} fp32 vectors, dim={wl.dim}, {wl.n_clusters:,} Gaussian clusters "
+            f"(sigma={wl.sigma}, centres U[-1,1]), unit-normalised, cosine eps={wl.eps}; "
+            f"ell={wl.ell}-bit sign strings, k={wl.k} blocks, d={wl.d} ({wl.masks} masks), Q={Q}")
+
+
+# ----------------------------------------------------------- clock sampler
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001 - clocks are best effort
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------- roofline helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_0904_3151_gb300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_0904_3151_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic(kind, st, n, dim, Q, W_words, passes):
+    """Algorithmic bytes of one launch of `kind` (averaged over its
+    launches in the step) -- the per-unit figures are derived in the design
+    notes."""
+    masks = st["masks"] // max(1, Q)
+    items = masks * n                      # grouped items per replicate batch
+    if kind == "radix_scatter":
+        per_item = (8 * W_words + 8 + (passes - 1) * 16) / passes
+        return items * per_item, "GB/s", "hbm"
+    if kind == "radix_hist":
+        per_item = (8 * W_words + (passes - 1) * 4) / passes
+        return items * per_item, "GB/s", "hbm"
+    if kind == "recheck":
+        return st["cand"] * (8 + 2 * 4 * dim + 12), "GB/s", "hbm"
+    return None, None, None
+
+
+def traffic_for(kind, workload):
+    """Measured DRAM bytes per launch from a committed ncu summary, if the
+    kernels have not changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except ValueError:
+        return None
+    e = d.get(kind)
+    if not e or e.get("source_hash") != kernel_source_hash() or e.get("workload") != workload:
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_oracle_run(X, R, wl, n_s):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.eps_graph(X[:n_s], R, wl.ell, wl.k, wl.d, oracle.COSINE, wl.eps)
+    return time.perf_counter() - t0
+
+
+def run_reference(a, wl, Q):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = a.n or wl.n
+    n_s = min(n, a.cpu_sample)
+    X = W.clustered(n, wl.dim, wl.n_clusters, wl.sigma, wl.data_seed)[:n_s]
+    import oracle
+    R = oracle.gaussian(wl.r_seed, Q * wl.dim * wl.ell).reshape(Q, wl.dim, wl.ell)
+    for _ in range(a.warmup):
+        cpu_oracle_run(X, R, wl, n_s)
+    t = 0.0
+    for _ in range(a.steps):
+        t += cpu_oracle_run(X, R, wl, n_s)
+    ms = 1000.0 * t / a.steps
+    value = n_s / (ms / 1000.0)
+    sample = (f"first {n_s:,} points of the {n:,}-point workload (same distribution, "
+              f"same R, Q={Q}); single-threaded C oracle, double precision")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(wl, n, Q), "n": n, "dim": wl.dim, "Q": Q,
+                   "sample_points": n_s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ main
+def main():
+    a = parse()
+    wl = W.WORKLOADS["scale"]
+    Q = a.Q
+    if a.impl == "reference":
+        return run_reference(a, wl, Q)
+
+    import torch
+    import paper_0904_3151_gb300 as msm
+    from paper_0904_3151_gb300 import build as b
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(b.LIB):
+        b.build()
+    if dist:
+        dist.barrier()
+    L = msm.lib()
+
+    n = a.n or wl.n
+    # weak scaling: every rank owns an independent point set of the workload
+    Xh = W.clustered(n, wl.dim, wl.n_clusters, wl.sigma, wl.data_seed + 7919 * rank)
+    X = torch.from_numpy(Xh).cuda()
+    seed = wl.r_seed
+    stream = torch.cuda.current_stream()
+
+    def step(xin):
+        return msm.eps_graph(xin, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=Q, seed=seed,
+                             cand_capacity=600 * n)
+
+    for _ in range(max(3, a.warmup)):
+        p, dv, st = step(X)
+        del p, dv
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = L.msm_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms = {}
+    klaunch = {}
+    counts = []
+    e0.record(stream)
+    for _ in range(a.steps):
+        p, dv, st = step(X)
+        counts.append(st["count"])
+        for kname, v in st["kernel_ms"].items():
+            kms[kname] = kms.get(kname, 0.0) + v
+            klaunch[kname] = klaunch.get(kname, 0) + st["kernel_launches"][kname]
+        del p, dv
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = L.msm_launch_count() - launches0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms / 1000.0)
+    pairs_per_s = world * counts[-1] / (ms / 1000.0)
+
+    # ---- e2e: host X in, host pairs out, through the same API
+    e2e = None
+    if not a.no_e2e:
+        Xpin = torch.from_numpy(Xh).pin_memory()
+        reps = max(2, min(3, a.steps))
+        p, dv, st = step(Xpin)          # warm
+        out_p = torch.empty(p.numel(), dtype=torch.int64, pin_memory=True)
+        out_d = torch.empty(dv.numel(), dtype=torch.float32, pin_memory=True)
+        del p, dv
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        bo = 0
+        for _ in range(reps):
+            p, dv, st = step(Xpin)
+            if out_p.numel() < p.numel():
+                out_p = torch.empty(p.numel(), dtype=torch.int64, pin_memory=True)
+                out_d = torch.empty(dv.numel(), dtype=torch.float32, pin_memory=True)
+            out_p[:p.numel()].copy_(p, non_blocking=True)
+            out_d[:dv.numel()].copy_(dv, non_blocking=True)
+            bo = p.numel() * 8 + dv.numel() * 4
+            del p, dv
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1) / reps
+        if dist:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * n / (ems / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": int(Xh.nbytes), "d2h_bytes_per_step": int(bo),
+               "ms_per_step": ems}
+
+    # ---- roofline of the dominant kernel class
+    peaks = measured_peaks()
+    W_words = (wl.ell + 63) // 64
+    passes = 4
+    dom = max(kms, key=lambda k: kms[k]) if kms else None
+    roof = None
+    hbm_kernels = {}
+    for kind in ("radix_scatter", "radix_hist", "recheck"):
+        if klaunch.get(kind):
+            bytes_per_launch, u, bound = algorithmic(kind, st, n, wl.dim, Q, W_words, passes)
+            avg_ms = kms[kind] / klaunch[kind]
+            ach = bytes_per_launch / (avg_ms / 1000.0) / 1e9
+            hbm_kernels[kind] = {"achieved": ach, "frac": ach / peaks["hbm_gbs"],
+                                 "avg_launch_ms": avg_ms, "launches_per_step": klaunch[kind] // a.steps}
+    if dom in hbm_kernels:
+        h = hbm_kernels[dom]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": h["achieved"], "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": h["frac"], "traffic": traffic_for(dom, "scale"),
+                "peak_source": peaks["source"]}
+    elif dom == "pair_check":
+        # integer-ALU bound: pair inspections per second against the
+        # issue-rate ceiling derived in the design notes
+        checks = st["checks"]
+        avg_ms = kms[dom] / klaunch[dom]
+        per_launch = checks / max(1, klaunch[dom] // a.steps)
+        ach = per_launch / (avg_ms / 1000.0) / 1e9
+        ops_per_check = 12
+        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = sm_count * 128 * peaks["sm_max_mhz"] * 1e6 / ops_per_check / 1e9
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak,
+                "unit": "Gchecks/s", "frac": ach / peak, "traffic": traffic_for(dom, "scale"),
+                "peak_source": f"derived: {sm_count} SMs x 128 int lanes x {peaks['sm_max_mhz']:.0f} MHz"
+                               f" / {ops_per_check} ops per check"}
+    elif dom == "project":
+        flops = 2.0 * n * wl.dim * Q * wl.ell
+        avg_ms = kms[dom] / klaunch[dom]
+        ach = flops / (avg_ms / 1000.0) / 1e12
+        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = sm_count * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": traffic_for(dom, "scale"),
+                "peak_source": "derived FP32 FMA issue rate"}
+
+    # ---- missing-edge ratio against exhaustive truth (outside timing)
+    missing = None
+    if not a.no_missing:
+        truth = msm.eps_count_exhaustive(X, msm.COSINE, wl.eps)
+        missing = {"truth_pairs": truth, "found_pairs": counts[-1],
+                   "ratio": (truth - counts[-1]) / max(1, truth)}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        n_s = min(n, a.cpu_sample)
+        R = oracle.gaussian(seed, Q * wl.dim * wl.ell).reshape(Q, wl.dim, wl.ell)
+        t = cpu_oracle_run(Xh, R, wl, n_s)
+        cpu = {"value": n_s / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {n_s:,} of the {n:,} points, same R and Q={Q}; "
+                         f"single-threaded C oracle, {t:.1f} s"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": max(3, a.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(wl, n, Q), "n_per_gpu": n, "dim": wl.dim,
+                       "ell": wl.ell, "k": wl.k, "d": wl.d, "Q": Q, "eps": wl.eps,
+                       "metric": "cosine", "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (X = 512 MB per GPU; grouping buffers ~3 GB)"},
+            "pairs_per_s": pairs_per_s, "pairs": counts[-1],
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roof, "hbm_kernels": hbm_kernels,
+            "kernel_ms_per_step": {k: v / a.steps for k, v in kms.items()},
+            "stats": {k: st[k] for k in ("Q", "masks", "checks", "cand", "type1",
+                                         "proj_recompute", "dist_recompute", "overflow_retries")},
+            "missing_edges": missing, "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * msm.h -- C ABI of the GB300 epsilon-neighbour-graph library.
+ *
+ * Method: Uno, Sugiyama and Tsuda, "Efficient Construction of Neighborhood
+ * Graphs by the Multiple Sorting Method".  Points are mapped to ell-bit
+ * strings by sign random projection (Sec. 3.2, Eq. 3), repeated for Q
+ * independent replicates (Sec. 4.1); the multiple sorting method with
+ * blockwise masking (Sec. 2.2) enumerates, per replicate, all string pairs
+ * within Hamming distance d (Eq. 5); the union of candidates is then checked
+ * against the exact distance (Sec. 4.1, last step).
+ *
+ * General rules for every entry point:
+ *   - Pointers documented "device" must be CUDA device (or managed) memory of
+ *     the current device; "host" pointers are ordinary CPU memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; calls that must read a count back
+ *     (documented) synchronise on it before returning.
+ *   - Inputs are never modified.  Return value is MSM_OK or a negative
+ *     MSM_E_* code; msm_last_error() gives a message for the calling thread.
+ *   - Pair encoding: (uint64_t)i << 32 | j with 0 <= i < j < n.
+ *   - String layout: replicate-major [Q][n][W] uint64 words, W = ceil(ell/64);
+ *     bit c of a string is bit (c & 63) of word (c >> 6); bits >= ell are 0.
+ *   - Blocks: block b (0-based, b < k) covers bits [floor(b*ell/k),
+ *     floor((b+1)*ell/k)).
+ *   - Limits: 1 <= ell <= 256, 1 <= k <= min(ell, 32), 0 <= d < k,
+ *     2 <= n < 2^31, 1 <= dim <= 4096.
+ */
+#ifndef MSM_H
+#define MSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define MSM_OK 0
+#define MSM_E_INVAL (-1)     /* argument outside the documented limits */
+#define MSM_E_NOMEM (-2)     /* an allocation failed */
+#define MSM_E_OVERFLOW (-3)  /* a caller-sized output is too small */
+#define MSM_E_CUDA (-4)      /* a CUDA runtime call or launch failed */
+#define MSM_E_TIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define MSM_E_ZERO_NORM (-6) /* cosine metric with an all-zero row */
+#define MSM_E_NONFINITE (-7) /* NaN or Inf in the input vectors */
+
+/* ---- element types of X ---- */
+#define MSM_DT_F32 0
+#define MSM_DT_BF16 1
+
+/* ---- metrics ---- */
+#define MSM_COSINE 0    /* Eq. 2: 1 - x_i.x_j / (|x_i| |x_j|) */
+#define MSM_EUCLIDEAN 1 /* |x_i - x_j|_2 */
+
+/* ---- output modes of msm_eps_graph ---- */
+#define MSM_OUT_PAIRS_DIST 0 /* pairs and float distances */
+#define MSM_OUT_PAIRS 1      /* pairs only (dist = NULL) */
+#define MSM_OUT_COUNT 2      /* count only (pairs = dist = NULL) */
+
+/* ---- flags ---- */
+#define MSM_FLAG_CANONICAL 1 /* sort output pairs ascending (i, then j) */
+
+/* Device memory provider.  alloc(bytes, stream, ctx) returns device memory
+ * usable in stream order on `stream` (NULL on failure); free(ptr, stream,
+ * ctx) releases it in stream order.  Scratch memory is freed before the
+ * call returns; output buffers (msm_pairs) stay alive and belong to the
+ * caller, who releases them with the same allocator (msm_free_pairs).
+ * A NULL allocator selects cudaMallocAsync / cudaFreeAsync on `stream`. */
+typedef struct msm_allocator {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} msm_allocator;
+
+/* A pair list produced by the library (device memory from the allocator). */
+typedef struct msm_pairs {
+  uint64_t* pairs; /* device [count], (i << 32) | j, i < j; NULL if count 0 */
+  float* dist;     /* device [count] or NULL (see output modes)            */
+  int64_t count;
+} msm_pairs;
+
+/* Counters and per-phase device times of one call (all optional). */
+typedef struct msm_stats {
+  int64_t Q;              /* replicates used                                  */
+  int64_t masks;          /* (replicate, kept-block set) groupings performed  */
+  int64_t checks;         /* pairs inspected inside groups of equal keys      */
+  int64_t cand;           /* |E| = |E_1 u ... u E_Q| (Sec. 4.1)               */
+  int64_t type1;          /* |E| - result size: type-I errors removed (4.2)   */
+  int64_t proj_recompute; /* projection signs decided in double precision     */
+  int64_t dist_recompute; /* epsilon comparisons decided in double precision  */
+  int64_t overflow_retries; /* candidate-buffer regrowths                     */
+  float ms[8]; /* device ms: 0 norms+R, 1 projection, 2 grouping sorts,
+                  3 group boundaries, 4 in-group checks, 5 recheck,
+                  6 canonical sort, 7 whole call                             */
+  /* Per kernel class, summed over the call's launches (CUDA events around
+   * each launch): 0 projection, 1 radix histogram, 2 radix scatter,
+   * 3 scans, 4 group boundaries, 5 in-group pair check, 6 recheck,
+   * 7 other (norms, generator, canonical sort). */
+  float kernel_ms[8];
+  int64_t kernel_launches[8];
+} msm_stats;
+
+/* Parameters of msm_eps_graph. */
+typedef struct msm_params {
+  int ell;  /* string length in bits (Sec. 3.2)                         */
+  int k;    /* blocks per string (Sec. 2.2)                             */
+  int d;    /* Hamming threshold = masked blocks per grouping (Sec. 2.2) */
+  int Q;    /* replicates; 0 = smallest Q meeting miss_ratio (Sec. 4.3) */
+  uint64_t seed;     /* seed of R when R == NULL (msm_gaussian)         */
+  const float* R;    /* optional device [Q][dim][ell] float projection  */
+  int out_mode;      /* MSM_OUT_*                                       */
+  int flags;         /* MSM_FLAG_*                                      */
+  int group_bits;    /* grouping-key width 8..32; 0 = automatic         */
+  int reserved;
+  int64_t cand_capacity; /* initial candidate buffer (pairs); 0 = auto */
+} msm_params;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int msm_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all devices); a diagnostic for launch accounting. */
+int64_t msm_launch_count(void);
+
+/* Message for a status code, and the last error message of this thread. */
+const char* msm_strerror(int status);
+const char* msm_last_error(void);
+
+/* Sec. 4.2: non-collision probability of one sign bit at the radius:
+ * p = arccos(1 - eps) / pi for MSM_COSINE; for MSM_EUCLIDEAN on unit
+ * vectors |x - y|^2 = 2 (cosine distance) (Sec. 5.1), so
+ * p = arccos(1 - eps^2 / 2) / pi.  Returns -1 for an invalid eps. */
+double msm_collision_p(int metric, double eps);
+
+/* Sec. 4.2 bound on the expected missing-edge ratio,
+ * (1 - sum_{t=0}^{d} C(ell, t) p^t (1 - p)^(ell - t))^Q.  Returns -1 on
+ * invalid arguments. */
+double msm_miss_bound(int ell, int d, double p, int Q);
+
+/* Sec. 4.3: smallest Q >= 1 whose bound is <= gamma, written to *Q.
+ * MSM_E_INVAL if gamma <= 0, p outside [0, 1), or no Q <= 2^24 suffices. */
+int msm_solve_Q(int ell, int d, double p, double gamma, int* Q);
+
+/* Step A0' (Sec. 3.2: R has i.i.d. N(0, 1) entries).  Writes `count`
+ * standard normal floats to device `out`: element e comes from block e/4 of
+ * the counter-based generator Philox4x64-10 (Salmon et al., SC 2011) with
+ * counter {e/4, 0, 0, 0} and key {seed, 0}; the block's words (w0, w1) and
+ * (w2, w3) feed two Box-Muller pairs, evaluated in double precision and
+ * rounded to float.  Asynchronous. */
+int msm_gaussian(uint64_t seed, int64_t count, float* out, void* stream);
+
+/* Step A1, Eq. 3: strings[q][i] bit c = 1 iff r_{q,c}^T x_i > 0.
+ *   X        device [n][dim], element type `dtype` (row-major, rows packed)
+ *   R        device [Q][dim][ell] float, or NULL to draw it with msm_gaussian
+ *            from `seed` (R_q is the q-th [dim][ell] block)
+ *   strings  device [Q][n][W] uint64, caller-owned, fully overwritten
+ *   recomputed  optional host pointer: number of signs decided in double
+ *            precision because the float result lay within its rounding-error
+ *            bound of zero (synchronises on `stream` when non-NULL)
+ * The sign of every bit equals the sign of the double-precision dot product
+ * accumulated by sequential fma over the dim coordinates.
+ * Scratch (only when R == NULL) comes from cudaMallocAsync. */
+int msm_project(const void* X, int64_t n, int dim, int dtype, const float* R,
+                uint64_t seed, int ell, int Q, uint64_t* strings,
+                int64_t* recomputed, void* stream);
+
+/* Steps A3-A7 (Sec. 2.2, Eq. 5, Appendix): every pair (i, j), i < j, whose
+ * strings lie within Hamming distance d in at least one of the Q pools,
+ * reported once.
+ *   strings  device [Q][n][W] uint64 (layout above)
+ *   out      receives the pair list (dist = NULL), allocated with `alloc`;
+ *            ascending when flags has MSM_FLAG_CANONICAL
+ *   stats    optional host pointer
+ * Synchronises on `stream` (counts are read back). */
+int msm_enumerate(const uint64_t* strings, int64_t n, int ell, int k, int d,
+                  int Q, int flags, const msm_allocator* alloc,
+                  msm_pairs* out, msm_stats* stats, void* stream);
+
+/* Step A8 (Sec. 4.1, last step): keep the candidate pairs whose distance is
+ * <= eps (inclusive, Def. 1.1).
+ *   X         device [n][dim] of `dtype`
+ *   cand      device [m] candidate pairs (any order, i < j < n)
+ *   pairs_out device [m] capacity, caller-owned; dist_out device [m] or NULL
+ *   count     host pointer, receives the number kept (synchronises)
+ *   recomputed optional host pointer: comparisons decided in double
+ * Every decision equals the one made on the double-precision distance of
+ * Eq. 2 (cosine) or the Euclidean norm, accumulated by sequential fma;
+ * returned distances are within 1e-5 relative of that value.  Output order
+ * is unspecified.  MSM_E_ZERO_NORM for a zero row under MSM_COSINE. */
+int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
+                float eps, const uint64_t* cand, int64_t m,
+                uint64_t* pairs_out, float* dist_out, int64_t* count,
+                int64_t* recomputed, void* stream);
+
+/* The whole method (Sec. 4.1): projection, blockwise MSM over Q replicates
+ * with replicate de-duplication, epsilon recheck.
+ *   X          host or device [n][dim] of `dtype` (host memory is copied in)
+ *   metric     MSM_COSINE or MSM_EUCLIDEAN; eps the radius
+ *   miss_ratio gamma of Sec. 4.3, used only when params->Q == 0
+ *   params     string geometry and options (see msm_params)
+ *   out        receives the result (see output modes), allocated with
+ *              `alloc`; count is always set
+ *   stats      optional host pointer
+ * Synchronises on `stream`. */
+int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
+                  float eps, double miss_ratio, const msm_params* params,
+                  const msm_allocator* alloc, msm_pairs* out,
+                  msm_stats* stats, void* stream);
+
+/* Release the buffers of a msm_pairs returned by this library. */
+void msm_free_pairs(msm_pairs* p, const msm_allocator* alloc, void* stream);
+
+/* Measurement aid, not part of the method: the exact number of pairs i < j
+ * with distance <= eps (Def. 1.1), by exhaustive comparison on the GPU with
+ * the same decision rule as msm_recheck.  Used to measure the missing-edge
+ * ratio of msm_eps_graph.  Synchronises. */
+int msm_eps_count_exhaustive(const void* X, int64_t n, int dim, int dtype,
+                             int metric, float eps, int64_t* count,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSM_H */

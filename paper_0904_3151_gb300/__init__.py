@@ -1,0 +1,215 @@
+"""GB300 epsilon-neighbour graphs by sign random projection + the multiple
+sorting method (Uno, Sugiyama, Tsuda).
+
+Thin Python binding over the C ABI of libmsm.so (include/msm.h): argument
+marshalling only.  Every step of the method runs in the library's CUDA
+kernels; PyTorch supplies device memory (through the allocator callback)
+and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import traceback
+
+import torch
+
+from . import _lib
+from ._lib import Allocator, Pairs, Params, Stats
+
+__all__ = ["MSMError", "gaussian", "project", "enumerate_pairs", "recheck",
+           "eps_graph", "eps_count_exhaustive", "collision_p", "miss_bound",
+           "solve_Q", "unpack_pairs", "COSINE", "EUCLIDEAN", "lib"]
+
+COSINE, EUCLIDEAN = 0, 1
+DT_F32, DT_BF16 = 0, 1
+OUT_PAIRS_DIST, OUT_PAIRS, OUT_COUNT = 0, 1, 2
+FLAG_CANONICAL = 1
+
+
+class MSMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        msg = L.msm_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {L.msm_strerror(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def lib():
+    return _lib.load()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise MSMError(status, where)
+
+
+def _metric(m) -> int:
+    if isinstance(m, str):
+        return {"cosine": COSINE, "euclidean": EUCLIDEAN}[m.lower()]
+    return int(m)
+
+
+def _dtype(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return DT_F32
+    if t.dtype == torch.bfloat16:
+        return DT_BF16
+    raise TypeError(f"unsupported element type {t.dtype}")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class _TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator."""
+
+    def __init__(self, device):
+        self.device = device
+        self.live = {}
+        self._a = _lib.ALLOC_FN(self._alloc)
+        self._f = _lib.FREE_FN(self._free)
+        self.struct = Allocator(self._a, self._f, None)
+
+    def _alloc(self, nbytes, stream, ctx):
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        except Exception:  # noqa: BLE001 - report as NULL to the library
+            traceback.print_exc()
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, ptr, stream, ctx):
+        self.live.pop(ptr, None)
+
+    def take(self, ptr, count, dtype):
+        """Hand a library-allocated buffer to the caller as a tensor."""
+        if not ptr:
+            return torch.empty(0, dtype=dtype, device=self.device)
+        t = self.live.pop(ptr)
+        return t.view(dtype)[:count]
+
+
+def gaussian(seed: int, count: int, device=None) -> torch.Tensor:
+    """Step A0': `count` N(0,1) floats from the counter-based generator."""
+    out = torch.empty(count, dtype=torch.float32, device=device or "cuda")
+    _check(lib().msm_gaussian(ctypes.c_uint64(seed), count, ctypes.c_void_p(out.data_ptr()),
+                              _stream()), "msm_gaussian")
+    return out
+
+
+def project(X: torch.Tensor, ell: int, Q: int, R: torch.Tensor | None = None,
+            seed: int = 0, return_recomputed: bool = False):
+    """Step A1 (Eq. 3): strings int64 view of uint64 [Q][n][ceil(ell/64)]."""
+    assert X.is_cuda and X.is_contiguous() and X.dim() == 2
+    n, dim = X.shape
+    if R is not None:
+        assert R.is_cuda and R.dtype == torch.float32 and R.is_contiguous()
+        assert tuple(R.shape) == (Q, dim, ell)
+    W = (ell + 63) // 64
+    S = torch.empty((Q, n, W), dtype=torch.int64, device=X.device)
+    rec = ctypes.c_int64(0)
+    _check(lib().msm_project(ctypes.c_void_p(X.data_ptr()), n, dim, _dtype(X),
+                             ctypes.c_void_p(R.data_ptr() if R is not None else 0),
+                             ctypes.c_uint64(seed), ell, Q, ctypes.c_void_p(S.data_ptr()),
+                             ctypes.byref(rec) if return_recomputed else None, _stream()),
+           "msm_project")
+    return (S, rec.value) if return_recomputed else S
+
+
+def enumerate_pairs(strings: torch.Tensor, ell: int, k: int, d: int,
+                    canonical: bool = False):
+    """Steps A3-A7: all pairs within Hamming d in at least one pool, once.
+    strings: int64/uint64 [Q][n][W] on the GPU.  Returns (pairs, stats)."""
+    assert strings.is_cuda and strings.is_contiguous() and strings.dim() == 3
+    Q, n, W = strings.shape
+    assert W == (ell + 63) // 64
+    A = _TorchAllocator(strings.device)
+    out = Pairs()
+    st = Stats()
+    _check(lib().msm_enumerate(ctypes.c_void_p(strings.data_ptr()), n, ell, k, d, Q,
+                               FLAG_CANONICAL if canonical else 0, ctypes.byref(A.struct),
+                               ctypes.byref(out), ctypes.byref(st), _stream()), "msm_enumerate")
+    pairs = A.take(out.pairs, out.count, torch.int64)
+    return pairs, st.as_dict()
+
+
+def recheck(X: torch.Tensor, cand: torch.Tensor, metric, eps: float):
+    """Step A8: keep the candidate pairs with distance <= eps.
+    Returns (pairs, dist, recomputed) in unspecified order."""
+    assert X.is_cuda and X.is_contiguous() and cand.is_cuda and cand.is_contiguous()
+    n, dim = X.shape
+    m = cand.numel()
+    pairs = torch.empty(max(m, 1), dtype=torch.int64, device=X.device)
+    dist = torch.empty(max(m, 1), dtype=torch.float32, device=X.device)
+    cnt = ctypes.c_int64(0)
+    rec = ctypes.c_int64(0)
+    _check(lib().msm_recheck(ctypes.c_void_p(X.data_ptr()), n, dim, _dtype(X), _metric(metric),
+                             ctypes.c_float(eps), ctypes.c_void_p(cand.data_ptr()), m,
+                             ctypes.c_void_p(pairs.data_ptr()), ctypes.c_void_p(dist.data_ptr()),
+                             ctypes.byref(cnt), ctypes.byref(rec), _stream()), "msm_recheck")
+    return pairs[:cnt.value], dist[:cnt.value], rec.value
+
+
+def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
+              Q: int = 0, miss_ratio: float = 1e-6, R: torch.Tensor | None = None,
+              seed: int = 0, out_mode: int = OUT_PAIRS_DIST, canonical: bool = False,
+              group_bits: int = 0, cand_capacity: int = 0, device=None):
+    """The whole method.  X may be a CUDA tensor or a (pinned) CPU tensor,
+    which the library copies in.  Returns (pairs, dist, stats)."""
+    assert X.is_contiguous() and X.dim() == 2
+    n, dim = X.shape
+    dev = X.device if X.is_cuda else torch.device(device or "cuda")
+    p = Params()
+    p.ell, p.k, p.d, p.Q = ell, k, d, Q
+    p.seed = seed
+    p.R = R.data_ptr() if R is not None else None
+    p.out_mode = out_mode
+    p.flags = FLAG_CANONICAL if canonical else 0
+    p.group_bits = group_bits
+    p.cand_capacity = cand_capacity
+    A = _TorchAllocator(dev)
+    out = Pairs()
+    st = Stats()
+    with torch.cuda.device(dev):
+        _check(lib().msm_eps_graph(ctypes.c_void_p(X.data_ptr()), n, dim, _dtype(X),
+                                   _metric(metric), ctypes.c_float(eps), ctypes.c_double(miss_ratio),
+                                   ctypes.byref(p), ctypes.byref(A.struct), ctypes.byref(out),
+                                   ctypes.byref(st), _stream()), "msm_eps_graph")
+    pairs = A.take(out.pairs, out.count, torch.int64) if out_mode != OUT_COUNT else None
+    dist = A.take(out.dist, out.count, torch.float32) if out_mode == OUT_PAIRS_DIST else None
+    s = st.as_dict()
+    s["count"] = int(out.count)
+    return pairs, dist, s
+
+
+def eps_count_exhaustive(X: torch.Tensor, metric, eps: float) -> int:
+    """Exact number of pairs within eps by exhaustive comparison (a
+    measurement aid for the missing-edge ratio)."""
+    assert X.is_cuda and X.is_contiguous()
+    n, dim = X.shape
+    c = ctypes.c_int64(0)
+    _check(lib().msm_eps_count_exhaustive(ctypes.c_void_p(X.data_ptr()), n, dim, _dtype(X),
+                                          _metric(metric), ctypes.c_float(eps), ctypes.byref(c),
+                                          _stream()), "msm_eps_count_exhaustive")
+    return c.value
+
+
+def collision_p(metric, eps: float) -> float:
+    return lib().msm_collision_p(_metric(metric), eps)
+
+
+def miss_bound(ell: int, d: int, p: float, Q: int) -> float:
+    return lib().msm_miss_bound(ell, d, p, Q)
+
+
+def solve_Q(ell: int, d: int, p: float, gamma: float) -> int:
+    q = ctypes.c_int(0)
+    _check(lib().msm_solve_Q(ell, d, p, gamma, ctypes.byref(q)), "msm_solve_Q")
+    return q.value
+
+
+def unpack_pairs(p: torch.Tensor):
+    return p >> 32, p & 0xFFFFFFFF

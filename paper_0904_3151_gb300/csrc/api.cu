@@ -1,0 +1,733 @@
+// C ABI entry points and host orchestration of the method:
+//   A0  replicate count from the missing-edge bound (Sec. 4.2 / 4.3)
+//   A0' Gaussian R (Sec. 3.2)          A1  projection + sign (Eq. 3)
+//   A3-A7 blockwise MSM per replicate (Sec. 2.2, Eq. 5, Appendix)
+//   A8  epsilon recheck (Sec. 4.1)     A9  optional canonical order
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "msm_internal.cuh"
+
+namespace msm {
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? MSM_E_NOMEM : MSM_E_CUDA;
+}
+
+// ------------------------------------------------------ launch accounting
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct KernelTimes {
+  struct Rec { int kc; cudaEvent_t b, e; };
+  std::vector<Rec> recs;
+  bool open = false;
+};
+static thread_local KernelTimes* g_kt = nullptr;
+
+void kt_begin(int kc, cudaStream_t s) {
+  if (!g_kt) return;
+  KernelTimes::Rec r{kc, nullptr, nullptr};
+  if (cudaEventCreate(&r.b) != cudaSuccess || cudaEventCreate(&r.e) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaEventRecord(r.b, s);
+  g_kt->recs.push_back(r);
+  g_kt->open = true;
+}
+
+void kt_end(cudaStream_t s) {
+  if (!g_kt || !g_kt->open) return;
+  cudaEventRecord(g_kt->recs.back().e, s);
+  g_kt->open = false;
+}
+
+KtScope::KtScope(bool on) : t(nullptr) {
+  if (on && !g_kt) {
+    t = new KernelTimes();
+    g_kt = t;
+  }
+}
+
+KtScope::~KtScope() {
+  if (!t) return;
+  for (auto& r : t->recs) {
+    cudaEventDestroy(r.b);
+    cudaEventDestroy(r.e);
+  }
+  if (g_kt == t) g_kt = nullptr;
+  delete t;
+}
+
+void KtScope::collect(float* ms, int64_t* launches) {
+  if (!t || t->recs.empty()) return;
+  cudaEventSynchronize(t->recs.back().e);
+  for (auto& r : t->recs) {
+    float v = 0.f;
+    if (cudaEventElapsedTime(&v, r.b, r.e) == cudaSuccess) ms[r.kc] += v;
+    else cudaGetLastError();
+    launches[r.kc] += 1;
+  }
+}
+
+int num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+// ------------------------------------------------------------------ memory
+void* raw_alloc(const msm_allocator* a, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (a && a->alloc) {
+    p = a->alloc(bytes, (void*)s, a->ctx);
+  } else {
+    static bool pool_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !pool_set[dev]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      pool_set[dev] = true;
+    }
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+  }
+  if (!p) set_error("device allocation of %zu bytes failed", bytes);
+  return p;
+}
+
+void raw_free(const msm_allocator* a, void* p, cudaStream_t s) {
+  if (!p) return;
+  if (a && a->free) a->free(p, (void*)s, a->ctx);
+  else cudaFreeAsync(p, s);
+}
+
+Scratch::~Scratch() {
+  for (int i = 0; i < nlive_; ++i) raw_free(a_, live_[i], s_);
+}
+
+void* Scratch::get(size_t bytes) {
+  if (nlive_ >= 64) {
+    set_error("too many scratch buffers");
+    return nullptr;
+  }
+  void* p = raw_alloc(a_, bytes, s_);
+  if (p) live_[nlive_++] = p;
+  return p;
+}
+
+void Scratch::put(void* p) {
+  for (int i = 0; i < nlive_; ++i)
+    if (live_[i] == p) {
+      raw_free(a_, p, s_);
+      live_[i] = live_[--nlive_];
+      return;
+    }
+}
+
+void Scratch::release(void* p) {
+  for (int i = 0; i < nlive_; ++i)
+    if (live_[i] == p) {
+      live_[i] = live_[--nlive_];
+      return;
+    }
+}
+
+// ------------------------------------------------------------------ layout
+BlockLayout make_layout(int ell, int k) {
+  BlockLayout L;
+  memset(&L, 0, sizeof(L));
+  L.ell = ell;
+  L.k = k;
+  L.W = (ell + 63) / 64;
+  for (int b = 0; b < k; ++b) {
+    int lo = (int)((int64_t)b * ell / k), hi = (int)((int64_t)(b + 1) * ell / k);
+    L.lo[b] = lo;
+    L.width[b] = hi - lo;
+    for (int c = lo; c < hi; ++c) L.mask[b][c >> 6] |= 1ull << (c & 63);
+  }
+  return L;
+}
+
+// Kept block sets of size r = k - d in lexicographic order (Sec. 2.2: every
+// choice of d masked blocks).
+static std::vector<MaskDesc> make_masks(const BlockLayout& L, int d) {
+  std::vector<MaskDesc> out;
+  int k = L.k, r = k - d;
+  std::vector<int> a(r);
+  for (int j = 0; j < r; ++j) a[j] = j;
+  while (true) {
+    MaskDesc m;
+    memset(&m, 0, sizeof(m));
+    for (int j = 0; j < r; ++j) {
+      int b = a[j];
+      m.K |= 1u << b;
+      m.kept_bits += L.width[b];
+      m.maxK = b;
+      for (int w = 0; w < kMaxWords; ++w) m.keep[w] |= L.mask[b][w];
+    }
+    out.push_back(m);
+    int i = r - 1;
+    while (i >= 0 && a[i] == k - r + i) --i;
+    if (i < 0) break;
+    ++a[i];
+    for (int j = i + 1; j < r; ++j) a[j] = a[j - 1] + 1;
+  }
+  return out;
+}
+
+static int check_geometry(int64_t n, int ell, int k, int d) {
+  if (n < 2 || n >= (1ll << 31)) return set_error("n must be in [2, 2^31)"), MSM_E_INVAL;
+  if (ell < 1 || ell > 256) return set_error("ell must be in [1, 256]"), MSM_E_INVAL;
+  if (k < 1 || k > ell || k > kMaxBlocks) return set_error("k must be in [1, min(ell, 32)]"), MSM_E_INVAL;
+  if (d < 0 || d >= k) return set_error("d must be in [0, k)"), MSM_E_INVAL;
+  double masks = 1.0;
+  for (int i = 0; i < d; ++i) masks = masks * (k - i) / (i + 1);
+  if (masks > 1e6) return set_error("C(k, d) = %.0f groupings is too many", masks), MSM_E_INVAL;
+  return MSM_OK;
+}
+
+// Event-based phase timer (only when stats are requested).
+struct PhaseTimer {
+  bool on;
+  cudaStream_t s;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> phase;
+  PhaseTimer(bool on_, cudaStream_t s_) : on(on_), s(s_) {}
+  ~PhaseTimer() { for (auto e : ev) cudaEventDestroy(e); }
+  void mark(int ph) {  // start of phase ph (-1 = end)
+    if (!on) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+    phase.push_back(ph);
+  }
+  void collect(float* ms) {
+    if (!on || ev.size() < 2) return;
+    cudaEventSynchronize(ev.back());
+    for (size_t i = 0; i + 1 < ev.size(); ++i) {
+      if (phase[i] < 0 || phase[i] > 6) continue;
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) ms[phase[i]] += t;
+    }
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ev.front(), ev.back()) == cudaSuccess) ms[7] = t;
+  }
+};
+
+template <typename T>
+static int read_back(T* host, const T* dev, cudaStream_t s) {
+  MSM_CUDA(cudaMemcpyAsync(host, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
+  MSM_CUDA(cudaStreamSynchronize(s));
+  return MSM_OK;
+}
+
+// A3-A7 over all replicates.  On success *cand (allocated from sc, owned by
+// sc) holds *count candidate pairs.
+static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
+                   int k, int d, int Q, int group_bits_req, int64_t cap0,
+                   uint64_t** cand_out, int64_t* count_out, msm_stats* st,
+                   PhaseTimer& tm) {
+  cudaStream_t s = sc.stream();
+  const BlockLayout L = make_layout(ell, k);
+  const std::vector<MaskDesc> masks = make_masks(L, d);
+  const int M = (int)masks.size();
+  int maxkept = 0;
+  for (const auto& m : masks) maxkept = m.kept_bits > maxkept ? m.kept_bits : maxkept;
+  int gb = group_bits_req;
+  if (gb <= 0) gb = maxkept <= 32 ? ((maxkept + 7) / 8) * 8 : 32;
+  if (gb < 8) gb = 8;
+  if (gb > 32) return set_error("group_bits must be <= 32"), MSM_E_INVAL;
+  const int passes = (gb + 7) / 8;
+  const int W = L.W;
+
+  // Masks per batch: bound the grouped items to 2^28.
+  int64_t Sb = ((int64_t)1 << 28) / n;
+  if (Sb < 1) Sb = 1;
+  if (Sb > M) Sb = M;
+
+  BlockLayout* dL = (BlockLayout*)sc.get(sizeof(BlockLayout));
+  MaskDesc* dM = (MaskDesc*)sc.get(sizeof(MaskDesc) * M);
+  unsigned long long* counters = (unsigned long long*)sc.get(256);
+  void* gws = sc.get(group_scratch_bytes(n, (int)Sb));
+  void* pws = sc.get(pairs_scratch_bytes(n * Sb));
+  if (!dL || !dM || !counters || !gws || !pws) return MSM_E_NOMEM;
+  MSM_CUDA(cudaMemcpyAsync(dL, &L, sizeof(L), cudaMemcpyHostToDevice, s));
+  MSM_CUDA(cudaMemcpyAsync(dM, masks.data(), sizeof(MaskDesc) * M, cudaMemcpyHostToDevice, s));
+  MSM_CUDA(cudaMemsetAsync(counters, 0, 256, s));
+  unsigned long long* count_dev = counters;
+  unsigned long long* checks_dev = counters + 1;
+
+  int64_t cap = cap0 > 0 ? cap0 : 16 * n;
+  uint64_t* cand = (uint64_t*)sc.get(8 * (size_t)cap);
+  if (!cand) return MSM_E_NOMEM;
+  int64_t count = 0, retries = 0;
+
+  for (int q = 0; q < Q; ++q) {
+    const uint64_t* pool = strings + (size_t)q * n * W;
+    for (int m0 = 0; m0 < M; m0 += (int)Sb) {
+      const int S = (int)((M - m0) < Sb ? (M - m0) : Sb);
+      GroupBatch gbt;
+      gbt.strings = pool;
+      gbt.n = n;
+      gbt.W = W;
+      gbt.masks = dM + m0;
+      gbt.S = S;
+      gbt.group_bits = gb;
+      gbt.passes = passes;
+      gbt.layout = dL;
+      uint32_t *keys = nullptr, *vals = nullptr;
+      tm.mark(2);
+      int rc = run_grouping(gbt, gws, &keys, &vals, s);
+      if (rc) return rc;
+      PairBatch pb;
+      pb.keys = keys;
+      pb.vals = vals;
+      pb.strings = strings;
+      pb.n = n;
+      pb.W = W;
+      pb.S = S;
+      pb.q = q;
+      pb.d = d;
+      pb.masks = dM + m0;
+      pb.layout = dL;
+      tm.mark(3);
+      rc = find_groups(pb, pws, checks_dev, s);
+      if (rc) return rc;
+      while (true) {
+        tm.mark(4);
+        rc = check_groups(pb, pws, cand, cap, count_dev, s);
+        if (rc) return rc;
+        tm.mark(-1);
+        unsigned long long c = 0;
+        rc = read_back(&c, count_dev, s);
+        if (rc) return rc;
+        if ((int64_t)c <= cap) {
+          count = (int64_t)c;
+          break;
+        }
+        // Candidate buffer too small: grow and redo this batch's checks.
+        int64_t ncap = (int64_t)c + (int64_t)c / 2 + 1024;
+        if (ncap < 2 * cap) ncap = 2 * cap;
+        uint64_t* nb = (uint64_t*)sc.get(8 * (size_t)ncap);
+        if (!nb) return MSM_E_NOMEM;
+        if (count > 0)
+          MSM_CUDA(cudaMemcpyAsync(nb, cand, 8 * (size_t)count, cudaMemcpyDeviceToDevice, s));
+        sc.put(cand);
+        cand = nb;
+        cap = ncap;
+        unsigned long long reset = (unsigned long long)count;
+        MSM_CUDA(cudaMemcpyAsync(count_dev, &reset, sizeof(reset), cudaMemcpyHostToDevice, s));
+        MSM_CUDA(cudaStreamSynchronize(s));
+        ++retries;
+      }
+    }
+  }
+  if (st) {
+    unsigned long long ch = 0;
+    int rc = read_back(&ch, checks_dev, s);
+    if (rc) return rc;
+    st->Q = Q;
+    st->masks = (int64_t)Q * M;
+    st->checks = (int64_t)ch;
+    st->cand = count;
+    st->overflow_retries = retries;
+  }
+  *cand_out = cand;
+  *count_out = count;
+  return MSM_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static size_t dtype_size(int dtype) { return dtype == MSM_DT_BF16 ? 2 : 4; }
+
+// Row norms + input validation.
+static int norms_and_check(Scratch& sc, const void* X, int dtype, int64_t n,
+                           int dim, int metric, double** nrm64, float** nrm32) {
+  cudaStream_t s = sc.stream();
+  *nrm64 = (double*)sc.get(8 * (size_t)n);
+  *nrm32 = (float*)sc.get(4 * (size_t)n);
+  unsigned* flags = (unsigned*)sc.get(256);
+  if (!*nrm64 || !*nrm32 || !flags) return MSM_E_NOMEM;
+  MSM_CUDA(cudaMemsetAsync(flags, 0, 4, s));
+  int rc = launch_row_norms(X, dtype, n, dim, *nrm64, *nrm32, flags, s);
+  if (rc) return rc;
+  unsigned f = 0;
+  rc = read_back(&f, flags, s);
+  if (rc) return rc;
+  if (f & 2u) return set_error("input contains NaN or Inf"), MSM_E_NONFINITE;
+  if ((f & 1u) && metric == MSM_COSINE)
+    return set_error("cosine distance is undefined for an all-zero row"), MSM_E_ZERO_NORM;
+  return MSM_OK;
+}
+
+static int bits_for(int64_t v) {
+  int b = 0;
+  while (b < 63 && ((int64_t)1 << b) <= v) ++b;
+  return b;
+}
+
+}  // namespace msm
+
+using namespace msm;
+
+// ======================================================================
+extern "C" {
+
+int msm_version(void) { return 100; }
+
+int64_t msm_launch_count(void) { return (int64_t)g_launches.load(); }
+
+const char* msm_strerror(int status) {
+  switch (status) {
+    case MSM_OK: return "ok";
+    case MSM_E_INVAL: return "invalid argument";
+    case MSM_E_NOMEM: return "out of device memory";
+    case MSM_E_OVERFLOW: return "output buffer too small";
+    case MSM_E_CUDA: return "CUDA error";
+    case MSM_E_TIMEOUT: return "device-side wait timed out";
+    case MSM_E_ZERO_NORM: return "zero-norm row under the cosine metric";
+    case MSM_E_NONFINITE: return "non-finite input value";
+    default: return "unknown status";
+  }
+}
+
+const char* msm_last_error(void) { return g_err; }
+
+double msm_collision_p(int metric, double eps) {
+  if (!(eps >= 0.0)) return -1.0;
+  double c = metric == MSM_EUCLIDEAN ? 1.0 - 0.5 * eps * eps : 1.0 - eps;
+  if (c < -1.0) c = -1.0;
+  if (c > 1.0) return -1.0;
+  return std::acos(c) / M_PI;
+}
+
+double msm_miss_bound(int ell, int d, double p, int Q) {
+  if (ell < 1 || d < 0 || Q < 1 || !(p >= 0.0 && p <= 1.0)) return -1.0;
+  // sum_{t<=d} C(ell,t) p^t (1-p)^(ell-t), terms by the ratio recurrence,
+  // added with Neumaier compensation.
+  double term = std::pow(1.0 - p, (double)ell);
+  double sum = 0.0, comp = 0.0;
+  int dd = d < ell ? d : ell;
+  for (int t = 0; t <= dd; ++t) {
+    if (t > 0) {
+      if (p == 1.0) term = (t == ell) ? 1.0 : 0.0;
+      else term = term * (double)(ell - t + 1) / (double)t * p / (1.0 - p);
+    }
+    double y = sum + term;
+    comp += std::fabs(sum) >= std::fabs(term) ? (sum - y) + term : (term - y) + sum;
+    sum = y;
+  }
+  double hit = sum + comp;
+  double miss = 1.0 - hit;
+  if (miss < 0.0) miss = 0.0;
+  return std::pow(miss, (double)Q);
+}
+
+int msm_solve_Q(int ell, int d, double p, double gamma, int* Q) {
+  if (!Q || !(gamma > 0.0) || !(p >= 0.0 && p < 1.0) || ell < 1 || d < 0)
+    return set_error("invalid arguments to msm_solve_Q"), MSM_E_INVAL;
+  double one = msm_miss_bound(ell, d, p, 1);
+  if (one <= gamma) { *Q = 1; return MSM_OK; }
+  if (one >= 1.0) return set_error("bound does not decrease with Q"), MSM_E_INVAL;
+  for (int q = 2; q <= (1 << 24); ++q)
+    if (std::pow(one, (double)q) <= gamma) { *Q = q; return MSM_OK; }
+  return set_error("no Q <= 2^24 meets the bound"), MSM_E_INVAL;
+}
+
+int msm_gaussian(uint64_t seed, int64_t count, float* out, void* stream) {
+  if (count < 0 || (count > 0 && !out)) return set_error("bad gaussian arguments"), MSM_E_INVAL;
+  return launch_gaussian(seed, count, out, (cudaStream_t)stream);
+}
+
+int msm_project(const void* X, int64_t n, int dim, int dtype, const float* R,
+                uint64_t seed, int ell, int Q, uint64_t* strings,
+                int64_t* recomputed, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!X || !strings || n < 1 || n >= (1ll << 31) || dim < 1 || dim > kMaxDim ||
+      ell < 1 || ell > 256 || Q < 1 || (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16))
+    return set_error("invalid msm_project arguments"), MSM_E_INVAL;
+  Scratch sc(nullptr, s);
+  const float* Rd = R;
+  if (!Rd) {
+    float* g = (float*)sc.get(4 * (size_t)Q * dim * ell);
+    if (!g) return MSM_E_NOMEM;
+    int rc = launch_gaussian(seed, (int64_t)Q * dim * ell, g, s);
+    if (rc) return rc;
+    Rd = g;
+  }
+  float* xn = (float*)sc.get(4 * (size_t)n);
+  float* rn = (float*)sc.get(4 * (size_t)Q * ell);
+  unsigned* flags = (unsigned*)sc.get(256);
+  unsigned long long* re = (unsigned long long*)(flags ? (char*)flags + 64 : nullptr);
+  if (!xn || !rn || !flags) return MSM_E_NOMEM;
+  MSM_CUDA(cudaMemsetAsync(flags, 0, 256, s));
+  int rc = launch_row_norms(X, dtype, n, dim, nullptr, xn, flags, s);
+  if (rc) return rc;
+  rc = launch_col_norms(Rd, Q, dim, ell, rn, s);
+  if (rc) return rc;
+  rc = launch_project(X, dtype, n, dim, Rd, rn, xn, Q, ell, strings, re, s);
+  if (rc) return rc;
+  if (recomputed) {
+    unsigned long long v = 0;
+    rc = read_back(&v, re, s);
+    if (rc) return rc;
+    *recomputed = (int64_t)v;
+  }
+  return MSM_OK;
+}
+
+int msm_enumerate(const uint64_t* strings, int64_t n, int ell, int k, int d,
+                  int Q, int flags, const msm_allocator* alloc,
+                  msm_pairs* out, msm_stats* stats, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!strings || !out || Q < 1) return set_error("invalid msm_enumerate arguments"), MSM_E_INVAL;
+  int rc = check_geometry(n, ell, k, d);
+  if (rc) return rc;
+  out->pairs = nullptr;
+  out->dist = nullptr;
+  out->count = 0;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  Scratch sc(alloc, s);
+  PhaseTimer tm(stats != nullptr, s);
+  KtScope kts(stats != nullptr);
+  tm.mark(2);
+  uint64_t* cand = nullptr;
+  int64_t m = 0;
+  rc = run_msm(sc, strings, n, ell, k, d, Q, 0, 0, &cand, &m, stats, tm);
+  if (rc) return rc;
+  if ((flags & MSM_FLAG_CANONICAL) && m > 1) {
+    tm.mark(6);
+    void* ws = sc.get(sort64_scratch_bytes(m));
+    if (!ws) return MSM_E_NOMEM;
+    rc = sort_pairs64(cand, nullptr, m, 32 + bits_for(n - 1), ws, s);
+    if (rc) return rc;
+  }
+  tm.mark(-1);
+  MSM_CUDA(cudaStreamSynchronize(s));
+  if (stats) {
+    tm.collect(stats->ms);
+    kts.collect(stats->kernel_ms, stats->kernel_launches);
+  }
+  sc.release(cand);
+  out->pairs = cand;
+  out->count = m;
+  return MSM_OK;
+}
+
+int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
+                float eps, const uint64_t* cand, int64_t m,
+                uint64_t* pairs_out, float* dist_out, int64_t* count,
+                int64_t* recomputed, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!X || !count || n < 2 || dim < 1 || dim > kMaxDim || m < 0 ||
+      (m > 0 && (!cand || !pairs_out)) || !(eps >= 0.f) ||
+      (metric != MSM_COSINE && metric != MSM_EUCLIDEAN) ||
+      (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16))
+    return set_error("invalid msm_recheck arguments"), MSM_E_INVAL;
+  Scratch sc(nullptr, s);
+  double* n64;
+  float* n32;
+  int rc = norms_and_check(sc, X, dtype, n, dim, metric, &n64, &n32);
+  if (rc) return rc;
+  unsigned long long* ctr = (unsigned long long*)sc.get(256);
+  if (!ctr) return MSM_E_NOMEM;
+  MSM_CUDA(cudaMemsetAsync(ctr, 0, 256, s));
+  rc = launch_recheck(X, dtype, n, dim, metric, eps, n64, cand, nullptr, m,
+                      pairs_out, dist_out, ctr, ctr + 1, s);
+  if (rc) return rc;
+  unsigned long long h[2] = {0, 0};
+  MSM_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MSM_CUDA(cudaStreamSynchronize(s));
+  *count = (int64_t)h[0];
+  if (recomputed) *recomputed = (int64_t)h[1];
+  return MSM_OK;
+}
+
+int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
+                  float eps, double miss_ratio, const msm_params* params,
+                  const msm_allocator* alloc, msm_pairs* out,
+                  msm_stats* stats, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!X || !params || !out || dim < 1 || dim > kMaxDim || !(eps >= 0.f) ||
+      (metric != MSM_COSINE && metric != MSM_EUCLIDEAN) ||
+      (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16) ||
+      params->out_mode < 0 || params->out_mode > 2)
+    return set_error("invalid msm_eps_graph arguments"), MSM_E_INVAL;
+  const int ell = params->ell, k = params->k, d = params->d;
+  int rc = check_geometry(n, ell, k, d);
+  if (rc) return rc;
+  int Q = params->Q;
+  if (Q <= 0) {
+    double p = msm_collision_p(metric, eps);
+    if (p < 0.0) return set_error("invalid eps"), MSM_E_INVAL;
+    rc = msm_solve_Q(ell, d, p, miss_ratio, &Q);
+    if (rc) return rc;
+  }
+  out->pairs = nullptr;
+  out->dist = nullptr;
+  out->count = 0;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  Scratch sc(alloc, s);
+  PhaseTimer tm(stats != nullptr, s);
+  KtScope kts(stats != nullptr);
+
+  // Input in device memory.
+  const void* Xd = X;
+  tm.mark(0);
+  if (!is_device_ptr(X)) {
+    void* buf = sc.get(dtype_size(dtype) * (size_t)n * dim);
+    if (!buf) return MSM_E_NOMEM;
+    MSM_CUDA(cudaMemcpyAsync(buf, X, dtype_size(dtype) * (size_t)n * dim, cudaMemcpyHostToDevice, s));
+    Xd = buf;
+  }
+  double* n64;
+  float* n32;
+  rc = norms_and_check(sc, Xd, dtype, n, dim, metric, &n64, &n32);
+  if (rc) return rc;
+  const float* R = params->R;
+  if (!R) {
+    float* g = (float*)sc.get(4 * (size_t)Q * dim * ell);
+    if (!g) return MSM_E_NOMEM;
+    rc = launch_gaussian(params->seed, (int64_t)Q * dim * ell, g, s);
+    if (rc) return rc;
+    R = g;
+  }
+  const int W = (ell + 63) / 64;
+  float* rn = (float*)sc.get(4 * (size_t)Q * ell);
+  uint64_t* strings = (uint64_t*)sc.get(8 * (size_t)Q * n * W);
+  unsigned long long* ctr = (unsigned long long*)sc.get(256);
+  if (!rn || !strings || !ctr) return MSM_E_NOMEM;
+  MSM_CUDA(cudaMemsetAsync(ctr, 0, 256, s));
+  rc = launch_col_norms(R, Q, dim, ell, rn, s);
+  if (rc) return rc;
+  tm.mark(1);
+  rc = launch_project(Xd, dtype, n, dim, R, rn, n32, Q, ell, strings, ctr + 2, s);
+  if (rc) return rc;
+
+  uint64_t* cand = nullptr;
+  int64_t m = 0;
+  rc = run_msm(sc, strings, n, ell, k, d, Q, params->group_bits,
+               params->cand_capacity, &cand, &m, stats, tm);
+  if (rc) return rc;
+  sc.put(strings);
+
+  // A8: recheck into the output buffers.
+  const int mode = params->out_mode;
+  uint64_t* pairs = nullptr;
+  float* dist = nullptr;
+  if (mode != MSM_OUT_COUNT && m > 0) {
+    pairs = (uint64_t*)sc.get(8 * (size_t)m);
+    if (!pairs) return MSM_E_NOMEM;
+    if (mode == MSM_OUT_PAIRS_DIST) {
+      dist = (float*)sc.get(4 * (size_t)m);
+      if (!dist) return MSM_E_NOMEM;
+    }
+  }
+  tm.mark(5);
+  rc = launch_recheck(Xd, dtype, n, dim, metric, eps, n64, cand, nullptr, m,
+                      pairs, dist, ctr, ctr + 1, s);
+  if (rc) return rc;
+  unsigned long long h[3] = {0, 0, 0};
+  MSM_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MSM_CUDA(cudaStreamSynchronize(s));
+  const int64_t kept = (int64_t)h[0];
+  sc.put(cand);
+  if ((params->flags & MSM_FLAG_CANONICAL) && pairs && kept > 1) {
+    tm.mark(6);
+    void* ws = sc.get(sort64_scratch_bytes(kept));
+    if (!ws) return MSM_E_NOMEM;
+    rc = sort_pairs64(pairs, (uint32_t*)dist, kept, 32 + bits_for(n - 1), ws, s);
+    if (rc) return rc;
+  }
+  tm.mark(-1);
+  MSM_CUDA(cudaStreamSynchronize(s));
+  if (stats) {
+    tm.collect(stats->ms);
+    kts.collect(stats->kernel_ms, stats->kernel_launches);
+    stats->type1 = m - kept;
+    stats->dist_recompute = (int64_t)h[1];
+    stats->proj_recompute = (int64_t)h[2];
+  }
+  if (pairs) sc.release(pairs);
+  if (dist) sc.release(dist);
+  out->pairs = pairs;
+  out->dist = dist;
+  out->count = kept;
+  return MSM_OK;
+}
+
+void msm_free_pairs(msm_pairs* p, const msm_allocator* alloc, void* stream) {
+  if (!p) return;
+  raw_free(alloc, p->pairs, (cudaStream_t)stream);
+  raw_free(alloc, p->dist, (cudaStream_t)stream);
+  p->pairs = nullptr;
+  p->dist = nullptr;
+  p->count = 0;
+}
+
+int msm_eps_count_exhaustive(const void* X, int64_t n, int dim, int dtype,
+                             int metric, float eps, int64_t* count,
+                             void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!X || !count || n < 2 || n >= (1ll << 31) || dim < 1 || dim > kMaxDim ||
+      !(eps >= 0.f) || (metric != MSM_COSINE && metric != MSM_EUCLIDEAN) ||
+      (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16))
+    return set_error("invalid msm_eps_count_exhaustive arguments"), MSM_E_INVAL;
+  Scratch sc(nullptr, s);
+  double* n64;
+  float* n32;
+  int rc = norms_and_check(sc, X, dtype, n, dim, metric, &n64, &n32);
+  if (rc) return rc;
+  unsigned long long* ctr = (unsigned long long*)sc.get(256);
+  if (!ctr) return MSM_E_NOMEM;
+  MSM_CUDA(cudaMemsetAsync(ctr, 0, 256, s));
+  rc = launch_eps_count(X, dtype, n, dim, metric, eps, n64, ctr, s);
+  if (rc) return rc;
+  unsigned long long c = 0;
+  rc = read_back(&c, ctr, s);
+  if (rc) return rc;
+  *count = (int64_t)c;
+  return MSM_OK;
+}
+
+}  // extern "C"

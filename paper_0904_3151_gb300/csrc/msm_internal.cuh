@@ -1,0 +1,176 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/msm.h"
+
+namespace msm {
+
+constexpr int kMaxWords = 4;    // ell <= 256
+constexpr int kMaxBlocks = 32;  // k <= 32 (block sets fit a uint32 mask)
+constexpr int kMaxDim = 4096;
+
+// Bit layout of the k blocks of an ell-bit string (Sec. 2.2: blocks of
+// approximately equal length).  Passed to kernels by value.
+struct BlockLayout {
+  int ell, k, W;
+  int lo[kMaxBlocks];
+  int width[kMaxBlocks];
+  uint64_t mask[kMaxBlocks][kMaxWords];
+};
+
+BlockLayout make_layout(int ell, int k);
+
+// One grouping (replicate q, kept block set K) of the multiple sorting
+// method; the grouping key of a string is its K blocks.
+struct MaskDesc {
+  uint64_t keep[kMaxWords];  // bits of the kept blocks
+  uint32_t K;                // kept blocks as a bit set
+  int kept_bits;             // number of kept bits
+  int maxK;                  // highest kept block index
+  int pad;
+};
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+#define MSM_CUDA(call)                                    \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return ::msm::cuda_fail(e_, #call); \
+  } while (0)
+#define MSM_LAUNCH(what)                                  \
+  do {                                                    \
+    cudaError_t e_ = cudaGetLastError();                  \
+    if (e_ != cudaSuccess) return ::msm::cuda_fail(e_, what); \
+    ::msm::count_launch();                                \
+  } while (0)
+
+int num_sms();
+
+// Kernel launch accounting: a process-wide launch counter, and (when a call
+// asked for statistics) CUDA events around every launch, summed per class.
+enum KernelClass {
+  KC_PROJECT = 0, KC_HIST = 1, KC_SCATTER = 2, KC_SCAN = 3,
+  KC_BOUNDS = 4, KC_CHECK = 5, KC_RECHECK = 6, KC_OTHER = 7
+};
+void count_launch();
+void kt_begin(int kc, cudaStream_t s);
+void kt_end(cudaStream_t s);
+struct KernelTimes;
+struct KtScope {  // installs a per-call timer for this thread
+  explicit KtScope(bool on);
+  ~KtScope();
+  void collect(float* ms, int64_t* launches);
+  KernelTimes* t;
+};
+
+// ------------------------------------------------------------ scratch
+// Device memory for one call: every buffer comes from the caller's
+// allocator (or cudaMallocAsync) and is released, stream-ordered, when the
+// Scratch goes out of scope, except buffers handed over with release().
+class Scratch {
+ public:
+  Scratch(const msm_allocator* a, cudaStream_t s) : a_(a), s_(s) {}
+  ~Scratch();
+  void* get(size_t bytes);          // NULL on failure (error message set)
+  void put(void* p);                // free now (stream-ordered)
+  void release(void* p);            // hand ownership to the caller
+  cudaStream_t stream() const { return s_; }
+  const msm_allocator* allocator() const { return a_; }
+ private:
+  const msm_allocator* a_;
+  cudaStream_t s_;
+  void* live_[64];
+  int nlive_ = 0;
+};
+
+void* raw_alloc(const msm_allocator* a, size_t bytes, cudaStream_t s);
+void raw_free(const msm_allocator* a, void* p, cudaStream_t s);
+
+// ------------------------------------------------------ kernel launchers
+// rng.cu
+int launch_gaussian(uint64_t seed, int64_t count, float* out, cudaStream_t s);
+
+// project.cu
+// Row norms in double (sequential fma of squares, then sqrt) plus a flag
+// word: bit 0 = some row has norm 0, bit 1 = some value is not finite.
+int launch_row_norms(const void* X, int dtype, int64_t n, int dim,
+                     double* nrm64, float* nrm32, unsigned* flags,
+                     cudaStream_t s);
+int launch_col_norms(const float* R, int Q, int dim, int ell, float* rn,
+                     cudaStream_t s);
+int launch_project(const void* X, int dtype, int64_t n, int dim,
+                   const float* R, const float* rnorm, const float* xnorm,
+                   int Q, int ell, uint64_t* strings,
+                   unsigned long long* recompute, cudaStream_t s);
+
+// group.cu: grouping of every (mask, string) of a batch of masks.
+struct GroupBatch {
+  const uint64_t* strings;  // the replicate's pool [n][W]
+  int64_t n;
+  int W;
+  const MaskDesc* masks;    // device [S]
+  int S;                    // masks in this batch
+  int group_bits;           // key width (8..32)
+  int passes;               // ceil(group_bits / 8)
+  const BlockLayout* layout;  // device copy
+};
+size_t group_scratch_bytes(int64_t n, int S);
+// Sorts (key, index) of all S*n items by key within each mask segment;
+// on return keys/vals hold the sorted order (pointers into `ws`).
+int run_grouping(const GroupBatch& b, void* ws, uint32_t** keys_out,
+                 uint32_t** vals_out, cudaStream_t s);
+// Generic exclusive scans (device-wide), returning the total in *total_dev.
+size_t scan_scratch_bytes(int64_t len);
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t len,
+                       void* ws, uint32_t* total_dev, cudaStream_t s);
+int exclusive_scan_u64(const uint64_t* in, uint64_t* out, int64_t len,
+                       void* ws, uint64_t* total_dev, cudaStream_t s);
+// Same, with the length read on the device (min(len_max, *len_dev)).
+int exclusive_scan_u64_devlen(const uint64_t* in, uint64_t* out,
+                              int64_t len_max, const uint32_t* len_dev,
+                              void* ws, uint64_t* total_dev, cudaStream_t s);
+// Radix sort of one segment of 64-bit keys with 32-bit payloads (used for
+// the canonical order of the output).
+size_t sort64_scratch_bytes(int64_t m);
+int sort_pairs64(uint64_t* keys, uint32_t* vals, int64_t m, int key_bits,
+                 void* ws, cudaStream_t s);
+
+// pairs.cu: group boundaries and the in-group pair check.
+struct PairBatch {
+  const uint32_t* keys;      // sorted keys [S*n]
+  const uint32_t* vals;      // point index of each sorted item [S*n]
+  const uint64_t* strings;   // all pools [Q][n][W]
+  int64_t n;
+  int W;
+  int S;
+  int q;                     // replicate of this batch
+  int d;
+  const MaskDesc* masks;     // device [S]
+  const BlockLayout* layout; // device copy
+};
+size_t pairs_scratch_bytes(int64_t items);
+// Finds the groups of >= 2 equal keys; returns on the device the number
+// of work items and adds sum C(size,2) to *checks_dev.
+int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
+                cudaStream_t s);
+// Checks every pair of every group and appends the pairs reported under
+// this (replicate, mask) to cand (capacity cap) at *count_dev.
+int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
+                 unsigned long long* count_dev, cudaStream_t s);
+
+// recheck.cu
+int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
+                   float eps, const double* nrm64, const uint64_t* cand,
+                   const unsigned long long* m_dev, int64_t m_max,
+                   uint64_t* pairs_out, float* dist_out,
+                   unsigned long long* count_dev,
+                   unsigned long long* recompute_dev, cudaStream_t s);
+int launch_eps_count(const void* X, int dtype, int64_t n, int dim, int metric,
+                     float eps, const double* nrm64,
+                     unsigned long long* count_dev, cudaStream_t s);
+
+}  // namespace msm

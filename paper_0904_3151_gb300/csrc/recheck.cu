@@ -1,0 +1,286 @@
+// Step A8 (Sec. 4.1, last step): exact distance test of each candidate pair
+// in E, keeping Delta(x_i, x_j) <= eps (Def. 1.1, inclusive).
+//
+// Fast path (float): S = sum_c (x_ic - x_jc)^2, each lane of an 8-lane group
+// summing its share of coordinates with compensated (Kahan) summation, then
+// a 3-level shuffle tree.  Every term carries at most 3 roundings
+// (difference, square, and the compensated sum's 2u) and the tree adds 3,
+// so |S' - S| <= 8u S + O(u^2) with u = 2^-24.
+//   Euclidean: Delta = sqrt(S).
+//   Cosine (Eq. 2): from |x_i - x_j|^2 = |x_i|^2 + |x_j|^2 - 2 x_i.x_j,
+//     Delta = (S - (|x_i| - |x_j|)^2) / (2 |x_i| |x_j|), norms in double;
+//     used only when (|x_i| - |x_j|)^2 <= S / 2, so the subtraction at most
+//     doubles the relative error.
+// A comparison whose float-path distance lies within its error bound (plus
+// the rounding error of the double-precision reference) of eps is decided
+// again on the double-precision distance evaluated exactly as Eq. 2 (or the
+// Euclidean norm) with sequential fma over the coordinates.
+#include <cuda_bf16.h>
+
+#include "msm_internal.cuh"
+
+namespace msm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr double kU = 0x1.0p-24;
+
+__device__ __forceinline__ float ldx(const void* X, int dtype, int64_t idx) {
+  if (dtype == MSM_DT_BF16)
+    return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(X)[idx]);
+  return reinterpret_cast<const float*>(X)[idx];
+}
+
+// Distance in double precision, same operation order as the definition:
+// cosine 1 - dot / (sqrt(|x_i|^2) * sqrt(|x_j|^2)), Euclidean sqrt(sum t^2).
+__device__ double exact_distance(const void* X, int dtype, int64_t i,
+                                 int64_t j, int dim, int metric) {
+  const int64_t bi = i * dim, bj = j * dim;
+  if (metric == MSM_COSINE) {
+    double dot = 0.0, ni = 0.0, nj = 0.0;
+    for (int c = 0; c < dim; ++c)
+      dot = fma((double)ldx(X, dtype, bi + c), (double)ldx(X, dtype, bj + c), dot);
+    for (int c = 0; c < dim; ++c) {
+      double v = (double)ldx(X, dtype, bi + c);
+      ni = fma(v, v, ni);
+    }
+    for (int c = 0; c < dim; ++c) {
+      double v = (double)ldx(X, dtype, bj + c);
+      nj = fma(v, v, nj);
+    }
+    return 1.0 - dot / (sqrt(ni) * sqrt(nj));
+  }
+  double s = 0.0;
+  for (int c = 0; c < dim; ++c) {
+    double t = (double)ldx(X, dtype, bi + c) - (double)ldx(X, dtype, bj + c);
+    s = fma(t, t, s);
+  }
+  return sqrt(s);
+}
+
+// Decision from the float-path sum S'.  Returns the distance to report and
+// sets *decided_exact when the double-precision reference was needed.
+__device__ __forceinline__ double decide(const void* X, int dtype, int64_t i,
+                                         int64_t j, int dim, int metric,
+                                         double eps, float S, double ni,
+                                         double nj, double relS, bool* keep,
+                                         bool* exact) {
+  double Sd = (double)S;
+  double delta, margin;
+  bool fallback = false;
+  if (metric == MSM_COSINE) {
+    double dn = ni - nj;
+    double T = dn * dn;
+    if (T > 0.5 * Sd) {
+      fallback = true;
+      delta = 0.0;
+      margin = 0.0;
+    } else {
+      double den = 2.0 * ni * nj;
+      delta = (Sd - T) / den;
+      // relative error of S' doubled by the subtraction, the norms' double
+      // rounding through T, and the reference's own rounding (dim + 8) 2^-52
+      margin = 2.5 * relS * delta + 8.0 * (ni + nj) * sqrt(Sd) * 0x1.0p-52 / den +
+               (double)(dim + 8) * 0x1.0p-51;
+    }
+  } else {
+    delta = sqrt(Sd);
+    margin = (0.5 * relS + (double)(dim + 4) * 0x1.0p-52) * delta + 1e-300;
+  }
+  if (fallback || fabs(delta - eps) <= margin) {
+    delta = exact_distance(X, dtype, i, j, dim, metric);
+    *exact = true;
+  } else {
+    *exact = false;
+  }
+  *keep = delta <= eps;
+  return delta;
+}
+
+// Sum of squared differences of rows i and j by the 8 lanes of a group.
+__device__ __forceinline__ float group_sq_dist(const void* X, int dtype,
+                                               int64_t i, int64_t j, int dim,
+                                               int sl) {
+  float acc = 0.f, comp = 0.f;
+  const int64_t bi = i * dim, bj = j * dim;
+  if (dtype == MSM_DT_F32 && (dim & 3) == 0) {
+    const float4* xi = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + bi);
+    const float4* xj = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + bj);
+    for (int c4 = sl; c4 < dim / 4; c4 += 8) {
+      float4 a = __ldg(xi + c4), b = __ldg(xj + c4);
+      float t[4] = {a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float y = __fmul_rn(t[u], t[u]) - comp;
+        float s = acc + y;
+        comp = (s - acc) - y;
+        acc = s;
+      }
+    }
+  } else {
+    for (int c = sl; c < dim; c += 8) {
+      float t = ldx(X, dtype, bi + c) - ldx(X, dtype, bj + c);
+      float y = __fmul_rn(t, t) - comp;
+      float s = acc + y;
+      comp = (s - acc) - y;
+      acc = s;
+    }
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  return acc;
+}
+
+// 4 pairs per warp (8 lanes each), grid-stride over the candidates.
+__global__ void __launch_bounds__(kThreads)
+recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
+               double eps, const double* nrm64, const uint64_t* cand,
+               const unsigned long long* m_dev, int64_t m_max,
+               uint64_t* pairs_out, float* dist_out, unsigned long long* count,
+               unsigned long long* recompute, double relS) {
+  int64_t m = m_max;
+  if (m_dev) m = min(m, (int64_t)*m_dev);
+  const int lane = threadIdx.x & 31, sl = lane & 7, grp = lane >> 3;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long nre = 0;
+  for (int64_t base = warp * 4; base < m; base += nwarps * 4) {
+    int64_t t = base + grp;
+    bool valid = t < m;
+    uint64_t pr = valid ? cand[t] : 0;
+    int64_t i = (int64_t)(pr >> 32), j = (int64_t)(pr & 0xffffffffu);
+    float S = group_sq_dist(X, dtype, valid ? i : 0, valid ? j : 0, dim, sl);
+    bool keep = false, exact = false;
+    double delta = 0.0;
+    if (valid && sl == 0) {
+      double ni = metric == MSM_COSINE ? nrm64[i] : 0.0;
+      double nj = metric == MSM_COSINE ? nrm64[j] : 0.0;
+      delta = decide(X, dtype, i, j, dim, metric, eps, S, ni, nj, relS, &keep, &exact);
+      nre += exact;
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (bal) {
+      unsigned long long b0 = 0;
+      if (lane == 0) b0 = atomicAdd(count, (unsigned long long)__popc(bal));
+      b0 = __shfl_sync(0xffffffffu, b0, 0);
+      if (keep) {
+        unsigned long long slot = b0 + __popc(bal & ((1u << lane) - 1u));
+        if (pairs_out) pairs_out[slot] = pr;
+        if (dist_out) dist_out[slot] = (float)delta;
+      }
+    }
+  }
+  if (nre) atomicAdd(recompute, nre);
+}
+
+// Exhaustive count of pairs within eps: 64 x 64 tiles of the upper
+// triangle, each thread 4 x 4 pairs, sequential float accumulation of the
+// squared differences (error bound (dim + 5) u S), same decision rule.
+constexpr int TB = 64, TK = 32;
+__global__ void __launch_bounds__(256)
+eps_count_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
+                 double eps, const double* nrm64, unsigned long long* count,
+                 double relS) {
+  __shared__ float Xi[TB][TK + 1];
+  __shared__ float Xj[TB][TK + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t nb = (n + TB - 1) / TB;
+  const int64_t ntiles = nb * (nb + 1) / 2;
+  unsigned long long c = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int64_t J = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+    while (J * (J + 1) / 2 > tile) --J;
+    while ((J + 1) * (J + 2) / 2 <= tile) ++J;
+    int64_t I = tile - J * (J + 1) / 2;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int k0 = 0; k0 < dim; k0 += TK) {
+      for (int e = tid; e < TB * TK; e += 256) {
+        int r = e / TK, cc = e % TK;
+        int64_t ri = I * TB + r, rj = J * TB + r;
+        int kk = k0 + cc;
+        Xi[r][cc] = (ri < n && kk < dim) ? ldx(X, dtype, ri * dim + kk) : 0.f;
+        Xj[r][cc] = (rj < n && kk < dim) ? ldx(X, dtype, rj * dim + kk) : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < TK; ++kk) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = Xi[ty * 4 + a][kk];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Xj[tx * 4 + b][kk];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            float t = av[a] - bv[b];
+            acc[a][b] = fmaf(t, t, acc[a][b]);
+          }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        int64_t i = I * TB + ty * 4 + a, j = J * TB + tx * 4 + b;
+        if (i < n && j < n && i < j) {
+          double ni = metric == MSM_COSINE ? nrm64[i] : 0.0;
+          double nj = metric == MSM_COSINE ? nrm64[j] : 0.0;
+          bool keep, exact;
+          decide(X, dtype, i, j, dim, metric, eps, acc[a][b], ni, nj, relS, &keep, &exact);
+          c += keep;
+        }
+      }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((tid & 31) == 0 && c) atomicAdd(count, c);
+}
+
+}  // namespace
+
+int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
+                   float eps, const double* nrm64, const uint64_t* cand,
+                   const unsigned long long* m_dev, int64_t m_max,
+                   uint64_t* pairs_out, float* dist_out,
+                   unsigned long long* count_dev,
+                   unsigned long long* recompute_dev, cudaStream_t s) {
+  if (m_max <= 0) return MSM_OK;
+  int64_t warps = (m_max + 3) / 4;
+  int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
+  int64_t cap = (int64_t)num_sms() * 8;
+  if (grid > cap) grid = cap;
+  double relS = 10.0 * kU;
+  kt_begin(KC_RECHECK, s);
+  recheck_kernel<<<(int)grid, kThreads, 0, s>>>(X, dtype, n, dim, metric,
+                                                (double)eps, nrm64, cand, m_dev,
+                                                m_max, pairs_out, dist_out,
+                                                count_dev, recompute_dev, relS);
+  kt_end(s);
+  MSM_LAUNCH("recheck_kernel");
+  return MSM_OK;
+}
+
+int launch_eps_count(const void* X, int dtype, int64_t n, int dim, int metric,
+                     float eps, const double* nrm64,
+                     unsigned long long* count_dev, cudaStream_t s) {
+  int64_t nb = (n + TB - 1) / TB;
+  int64_t ntiles = nb * (nb + 1) / 2;
+  int64_t grid = (int64_t)num_sms() * 8;
+  if (grid > ntiles) grid = ntiles;
+  double relS = (double)(dim + 6) * kU;
+  kt_begin(KC_OTHER, s);
+  eps_count_kernel<<<(int)grid, 256, 0, s>>>(X, dtype, n, dim, metric,
+                                             (double)eps, nrm64, count_dev, relS);
+  kt_end(s);
+  MSM_LAUNCH("eps_count_kernel");
+  return MSM_OK;
+}
+
+}  // namespace msm

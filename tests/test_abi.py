@@ -1,0 +1,83 @@
+"""The C-ABI library builds, loads, and exports every symbol include/msm.h
+declares; the host-only entry points (replicate-count arithmetic of
+Sec. 4.2-4.3, error strings) agree with the oracle.  No GPU needed."""
+import math
+import os
+import re
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_0904_3151_gb300 import build as b
+    b.build()
+    import paper_0904_3151_gb300 as msm
+    return msm.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "msm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"^\s*(?:int|int64_t|double|void|const char\*)\s+(msm_\w+)\s*\(", src, flags=re.M))
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_0904_3151_gb300 import _lib
+    names = _declared()
+    assert len(names) >= 12
+    for nm in sorted(names):
+        assert hasattr(L, nm), nm
+    assert names == set(_lib.SIGNATURES), names ^ set(_lib.SIGNATURES)
+
+
+def test_version_and_strerror(L):
+    assert L.msm_version() >= 100
+    for code in [0, -1, -2, -3, -4, -5, -6, -7]:
+        assert L.msm_strerror(code)
+    assert L.msm_strerror(-99) == b"unknown status"
+
+
+def test_collision_p_matches_oracle(L):
+    for eps in [0.0, 0.0123, 0.1, 0.15, 0.7, 1.0, 1.9]:
+        assert L.msm_collision_p(0, eps) == pytest.approx(oracle.p_cosine(eps), rel=1e-14, abs=1e-15)
+    for eps in [0.0, 0.1, 0.3, 1.0]:
+        assert L.msm_collision_p(1, eps) == pytest.approx(oracle.p_euclidean(eps), rel=1e-14, abs=1e-15)
+    assert L.msm_collision_p(0, -0.5) == -1.0
+
+
+@pytest.mark.parametrize("ell,d", [(50, 0), (50, 3), (64, 4), (128, 6), (128, 8), (96, 4), (256, 20)])
+def test_miss_bound_and_solve_Q_match_oracle(L, ell, d):
+    import ctypes
+    for p in [0.01, 0.04, 0.1, 0.2]:
+        b1 = oracle.miss_bound(ell, d, p, 1)
+        for Q in [1, 3, 10]:
+            a = L.msm_miss_bound(ell, d, p, Q)
+            b = oracle.miss_bound(ell, d, p, Q)
+            # 1 - sum(...) carries ~1e-16 absolute rounding in either
+            # evaluation; raised to the power Q it scales by Q b1^(Q-1).
+            tol = Q * b1 ** (Q - 1) * 4e-16
+            assert a == pytest.approx(b, rel=1e-9, abs=tol + 1e-300)
+        for gamma in [1e-2, 1e-6]:
+            q = ctypes.c_int(0)
+            rc = L.msm_solve_Q(ell, d, p, gamma, ctypes.byref(q))
+            try:
+                want = oracle.solve_Q(ell, d, p, gamma)
+            except ValueError:       # beyond the oracle's 2^20 search range
+                assert rc != 0 or q.value > (1 << 20)
+                continue
+            assert rc == 0
+            if q.value != want:   # only a rounding tie at the threshold may differ
+                b1 = oracle.miss_bound(ell, d, p, min(q.value, want))
+                assert math.isclose(b1, gamma, rel_tol=1e-9)
+
+
+def test_solve_Q_rejects_bad_input(L):
+    import ctypes
+    q = ctypes.c_int(0)
+    assert L.msm_solve_Q(64, 4, 0.1, 0.0, ctypes.byref(q)) == -1
+    assert L.msm_solve_Q(64, 4, 1.5, 1e-3, ctypes.byref(q)) == -1
