@@ -60,6 +60,7 @@ extern "C" {
 
 /* ---- flags ---- */
 #define MSM_FLAG_CANONICAL 1 /* sort output pairs ascending (i, then j) */
+#define MSM_FLAG_SIMT_PROJECTION 2 /* project on CUDA cores, not tcgen05 */
 
 /* Device memory provider.  alloc(bytes, stream, ctx) returns device memory
  * usable in stream order on `stream` (NULL on failure); free(ptr, stream,
@@ -155,14 +156,17 @@ int msm_gaussian(uint64_t seed, int64_t count, float* out, void* stream);
  *   R        device [Q][dim][ell] float, or NULL to draw it with msm_gaussian
  *            from `seed` (R_q is the q-th [dim][ell] block)
  *   strings  device [Q][n][W] uint64, caller-owned, fully overwritten
+ *   flags    MSM_FLAG_SIMT_PROJECTION forces the CUDA-core kernel; otherwise
+ *            rows of 128/256/384/512 bytes with a 16-byte-aligned X use the
+ *            tcgen05 tensor-core kernel
  *   recomputed  optional host pointer: number of signs decided in double
- *            precision because the float result lay within its rounding-error
- *            bound of zero (synchronises on `stream` when non-NULL)
+ *            precision because a lower-precision result lay within its
+ *            rounding-error bound of zero (synchronises when non-NULL)
  * The sign of every bit equals the sign of the double-precision dot product
  * accumulated by sequential fma over the dim coordinates.
- * Scratch (only when R == NULL) comes from cudaMallocAsync. */
+ * Scratch comes from cudaMallocAsync; the call synchronises on `stream`. */
 int msm_project(const void* X, int64_t n, int dim, int dtype, const float* R,
-                uint64_t seed, int ell, int Q, uint64_t* strings,
+                uint64_t seed, int ell, int Q, int flags, uint64_t* strings,
                 int64_t* recomputed, void* stream);
 
 /* Steps A3-A7 (Sec. 2.2, Eq. 5, Appendix): every pair (i, j), i < j, whose

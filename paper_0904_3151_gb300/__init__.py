@@ -24,6 +24,7 @@ COSINE, EUCLIDEAN = 0, 1
 DT_F32, DT_BF16 = 0, 1
 OUT_PAIRS_DIST, OUT_PAIRS, OUT_COUNT = 0, 1, 2
 FLAG_CANONICAL = 1
+FLAG_SIMT_PROJECTION = 2
 
 
 class MSMError(RuntimeError):
@@ -101,7 +102,7 @@ def gaussian(seed: int, count: int, device=None) -> torch.Tensor:
 
 
 def project(X: torch.Tensor, ell: int, Q: int, R: torch.Tensor | None = None,
-            seed: int = 0, return_recomputed: bool = False):
+            seed: int = 0, return_recomputed: bool = False, simt: bool = False):
     """Step A1 (Eq. 3): strings int64 view of uint64 [Q][n][ceil(ell/64)]."""
     assert X.is_cuda and X.is_contiguous() and X.dim() == 2
     n, dim = X.shape
@@ -113,7 +114,8 @@ def project(X: torch.Tensor, ell: int, Q: int, R: torch.Tensor | None = None,
     rec = ctypes.c_int64(0)
     _check(lib().msm_project(ctypes.c_void_p(X.data_ptr()), n, dim, _dtype(X),
                              ctypes.c_void_p(R.data_ptr() if R is not None else 0),
-                             ctypes.c_uint64(seed), ell, Q, ctypes.c_void_p(S.data_ptr()),
+                             ctypes.c_uint64(seed), ell, Q, FLAG_SIMT_PROJECTION if simt else 0,
+                             ctypes.c_void_p(S.data_ptr()),
                              ctypes.byref(rec) if return_recomputed else None, _stream()),
            "msm_project")
     return (S, rec.value) if return_recomputed else S
@@ -156,7 +158,8 @@ def recheck(X: torch.Tensor, cand: torch.Tensor, metric, eps: float):
 def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
               Q: int = 0, miss_ratio: float = 1e-6, R: torch.Tensor | None = None,
               seed: int = 0, out_mode: int = OUT_PAIRS_DIST, canonical: bool = False,
-              group_bits: int = 0, cand_capacity: int = 0, device=None):
+              group_bits: int = 0, cand_capacity: int = 0, simt_projection: bool = False,
+              device=None):
     """The whole method.  X may be a CUDA tensor or a (pinned) CPU tensor,
     which the library copies in.  Returns (pairs, dist, stats)."""
     assert X.is_contiguous() and X.dim() == 2
@@ -167,7 +170,7 @@ def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
     p.seed = seed
     p.R = R.data_ptr() if R is not None else None
     p.out_mode = out_mode
-    p.flags = FLAG_CANONICAL if canonical else 0
+    p.flags = (FLAG_CANONICAL if canonical else 0) | (FLAG_SIMT_PROJECTION if simt_projection else 0)
     p.group_bits = group_bits
     p.cand_capacity = cand_capacity
     A = _TorchAllocator(dev)

@@ -67,7 +67,7 @@ SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_int)]),
     "msm_gaussian": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, vp, vp]),
     "msm_project": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, ctypes.c_uint64,
-                                   ctypes.c_int, ctypes.c_int, vp, i64p, vp]),
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, i64p, vp]),
     "msm_enumerate": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(Allocator),
                                      ctypes.POINTER(Pairs), ctypes.POINTER(Stats), vp]),

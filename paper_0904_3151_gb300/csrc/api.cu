@@ -196,6 +196,8 @@ static std::vector<MaskDesc> make_masks(const BlockLayout& L, int d) {
       m.maxK = b;
       for (int w = 0; w < kMaxWords; ++w) m.keep[w] |= L.mask[b][w];
     }
+    for (int b = 0; b < m.maxK; ++b)
+      if (!(m.K >> b & 1u)) m.gap[m.ngap++] = (uint8_t)b;
     out.push_back(m);
     int i = r - 1;
     while (i >= 0 && a[i] == k - r + i) --i;
@@ -320,6 +322,7 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
       pb.S = S;
       pb.q = q;
       pb.d = d;
+      pb.group_bits = gb;
       pb.masks = dM + m0;
       pb.layout = dL;
       tm.mark(3);
@@ -398,6 +401,37 @@ static int norms_and_check(Scratch& sc, const void* X, int dtype, int64_t n,
   if ((f & 1u) && metric == MSM_COSINE)
     return set_error("cosine distance is undefined for an all-zero row"), MSM_E_ZERO_NORM;
   return MSM_OK;
+}
+
+// A1: tensor-core projection where the row layout allows it, else (or on
+// queue overflow) the CUDA-core kernel.  rnorm: float [Q * ell] column norms
+// for the CUDA-core path (computed here when needed).
+static int run_projection(Scratch& sc, const void* X, int dtype, int64_t n,
+                          int dim, const float* R, const float* xnorm, int Q,
+                          int ell, int flags, uint64_t* strings,
+                          unsigned long long* recompute_dev) {
+  cudaStream_t s = sc.stream();
+  bool simt = (flags & MSM_FLAG_SIMT_PROJECTION) != 0 ||
+              !tc_project_supported(dtype, dim, (uintptr_t)X);
+  if (!simt) {
+    void* ws = sc.get(tc_project_scratch_bytes(n, dim, Q, ell, dtype));
+    unsigned* status = (unsigned*)sc.get(256);
+    if (!ws || !status) return MSM_E_NOMEM;
+    MSM_CUDA(cudaMemsetAsync(status, 0, 256, s));
+    bool fell_back = false;
+    int rc = launch_project_tc(X, dtype, n, dim, R, xnorm, Q, ell, strings,
+                               recompute_dev, ws, status, &fell_back, s);
+    sc.put(ws);
+    if (rc) return rc;
+    if (!fell_back) return MSM_OK;
+  }
+  float* rn = (float*)sc.get(4 * (size_t)Q * ell);
+  if (!rn) return MSM_E_NOMEM;
+  int rc = launch_col_norms(R, Q, dim, ell, rn, s);
+  if (rc) return rc;
+  rc = launch_project(X, dtype, n, dim, R, rn, xnorm, Q, ell, strings, recompute_dev, s);
+  sc.put(rn);
+  return rc;
 }
 
 static int bits_for(int64_t v) {
@@ -480,7 +514,7 @@ int msm_gaussian(uint64_t seed, int64_t count, float* out, void* stream) {
 }
 
 int msm_project(const void* X, int64_t n, int dim, int dtype, const float* R,
-                uint64_t seed, int ell, int Q, uint64_t* strings,
+                uint64_t seed, int ell, int Q, int flags, uint64_t* strings,
                 int64_t* recomputed, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (!X || !strings || n < 1 || n >= (1ll << 31) || dim < 1 || dim > kMaxDim ||
@@ -496,23 +530,18 @@ int msm_project(const void* X, int64_t n, int dim, int dtype, const float* R,
     Rd = g;
   }
   float* xn = (float*)sc.get(4 * (size_t)n);
-  float* rn = (float*)sc.get(4 * (size_t)Q * ell);
-  unsigned* flags = (unsigned*)sc.get(256);
-  unsigned long long* re = (unsigned long long*)(flags ? (char*)flags + 64 : nullptr);
-  if (!xn || !rn || !flags) return MSM_E_NOMEM;
-  MSM_CUDA(cudaMemsetAsync(flags, 0, 256, s));
-  int rc = launch_row_norms(X, dtype, n, dim, nullptr, xn, flags, s);
+  unsigned* fl = (unsigned*)sc.get(256);
+  unsigned long long* re = (unsigned long long*)(fl ? (char*)fl + 64 : nullptr);
+  if (!xn || !fl) return MSM_E_NOMEM;
+  MSM_CUDA(cudaMemsetAsync(fl, 0, 256, s));
+  int rc = launch_row_norms(X, dtype, n, dim, nullptr, xn, fl, s);
   if (rc) return rc;
-  rc = launch_col_norms(Rd, Q, dim, ell, rn, s);
+  rc = run_projection(sc, X, dtype, n, dim, Rd, xn, Q, ell, flags, strings, re);
   if (rc) return rc;
-  rc = launch_project(X, dtype, n, dim, Rd, rn, xn, Q, ell, strings, re, s);
+  unsigned long long v = 0;
+  rc = read_back(&v, re, s);
   if (rc) return rc;
-  if (recomputed) {
-    unsigned long long v = 0;
-    rc = read_back(&v, re, s);
-    if (rc) return rc;
-    *recomputed = (int64_t)v;
-  }
+  if (recomputed) *recomputed = (int64_t)v;
   return MSM_OK;
 }
 
@@ -633,15 +662,13 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
     R = g;
   }
   const int W = (ell + 63) / 64;
-  float* rn = (float*)sc.get(4 * (size_t)Q * ell);
   uint64_t* strings = (uint64_t*)sc.get(8 * (size_t)Q * n * W);
   unsigned long long* ctr = (unsigned long long*)sc.get(256);
-  if (!rn || !strings || !ctr) return MSM_E_NOMEM;
+  if (!strings || !ctr) return MSM_E_NOMEM;
   MSM_CUDA(cudaMemsetAsync(ctr, 0, 256, s));
-  rc = launch_col_norms(R, Q, dim, ell, rn, s);
-  if (rc) return rc;
   tm.mark(1);
-  rc = launch_project(Xd, dtype, n, dim, R, rn, n32, Q, ell, strings, ctr + 2, s);
+  rc = run_projection(sc, Xd, dtype, n, dim, R, n32, Q, ell, params->flags,
+                      strings, ctr + 2);
   if (rc) return rc;
 
   uint64_t* cand = nullptr;

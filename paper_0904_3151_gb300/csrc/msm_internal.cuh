@@ -30,7 +30,9 @@ struct MaskDesc {
   uint32_t K;                // kept blocks as a bit set
   int kept_bits;             // number of kept bits
   int maxK;                  // highest kept block index
-  int pad;
+  int ngap;                  // blocks below maxK that are not kept
+  uint8_t gap[kMaxBlocks];   // those blocks: a pair is reported under K only
+                             // if it differs in every one of them
 };
 
 // ---------------------------------------------------------------- errors
@@ -107,6 +109,19 @@ int launch_project(const void* X, int dtype, int64_t n, int dim,
                    int Q, int ell, uint64_t* strings,
                    unsigned long long* recompute, cudaStream_t s);
 
+// project_tc.cu: the same projection on tcgen05 tensor cores (TF32 for
+// float X, BF16 with a split R for bf16 X), TMA-fed, sign/pack in the TMEM
+// epilogue; undecided bits are queued and settled by a fix-up kernel.
+bool tc_project_supported(int dtype, int dim, uintptr_t xaddr);
+size_t tc_project_scratch_bytes(int64_t n, int dim, int Q, int ell, int dtype);
+// *fell_back = true when the queue overflowed (the caller must then run the
+// SIMT projection, which overwrites every string).
+int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
+                      const float* R, const float* xnorm, int Q, int ell,
+                      uint64_t* strings, unsigned long long* recompute,
+                      void* ws, unsigned* status, bool* fell_back,
+                      cudaStream_t s);
+
 // group.cu: grouping of every (mask, string) of a batch of masks.
 struct GroupBatch {
   const uint64_t* strings;  // the replicate's pool [n][W]
@@ -149,6 +164,8 @@ struct PairBatch {
   int S;
   int q;                     // replicate of this batch
   int d;
+  int group_bits;            // grouping-key width (keys are exact when the
+                             // kept bits fit)
   const MaskDesc* masks;     // device [S]
   const BlockLayout* layout; // device copy
 };

@@ -188,6 +188,7 @@ struct CheckArgs {
   int W;
   int q;
   int d;
+  int group_bits;
   const MaskDesc* masks;
   const BlockLayout* layout;
   uint64_t* cand;
@@ -195,54 +196,72 @@ struct CheckArgs {
   unsigned long long* count;
 };
 
+// The three tests of one pair, cheapest and most selective first.
+//   first-mask rule: K blocks equal (only in doubt when keys were hashed)
+//   and every gap block (below max K, not kept) different;
+//   Hamming <= d; no earlier replicate within d (Appendix).
 template <int W>
 __device__ __forceinline__ bool pair_ok(const CheckArgs& a,
-                                        const uint64_t (*bm)[W], uint32_t K,
-                                        int maxK, uint32_t i, uint32_t j,
+                                        const uint64_t (*gm)[W], int ngap,
+                                        const uint64_t* keep, bool hashed,
+                                        uint32_t i, uint32_t j,
                                         const uint64_t* si,
                                         const uint64_t* sj) {
   uint64_t x[W];
-  int h = 0;
 #pragma unroll
-  for (int w = 0; w < W; ++w) {
-    x[w] = si[w] ^ sj[w];
-    h += __popcll(x[w]);
-  }
-  if (h > a.d) return false;
-  // Equal-block set restricted to blocks <= maxK must be exactly K.
-  uint32_t e = 0;
-  for (int b = 0; b <= maxK; ++b) {
+  for (int w = 0; w < W; ++w) x[w] = si[w] ^ sj[w];
+  if (hashed) {
     uint64_t o = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) o |= x[w] & bm[b][w];
-    e |= (uint32_t)(o == 0) << b;
+    for (int w = 0; w < W; ++w) o |= x[w] & keep[w];
+    if (o) return false;
   }
-  if (e != K) return false;
-  // Appendix: drop the pair if an earlier replicate already finds it.
+  for (int gI = 0; gI < ngap; ++gI) {
+    uint64_t o = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) o |= x[w] & gm[gI][w];
+    if (o == 0) return false;
+  }
+  int h = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) h += __popcll(x[w]);
+  if (h > a.d) return false;
   for (int g = 0; g < a.q; ++g) {
     const uint64_t* gi = a.strings + ((size_t)g * a.n + i) * W;
     const uint64_t* gj = a.strings + ((size_t)g * a.n + j) * W;
     int hg = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) hg += __popcll(gi[w] ^ gj[w]);
+    for (int w = 0; w < W; ++w) hg += __popcll(__ldg(gi + w) ^ __ldg(gj + w));
     if (hg <= a.d) return false;
   }
   return true;
 }
 
-__device__ __forceinline__ void emit(const CheckArgs& a, bool pass, uint32_t i,
-                                     uint32_t j, int lane) {
-  unsigned bal = __ballot_sync(0xffffffffu, pass);
-  if (bal == 0) return;
+// Appends, for every set bit c of `mask`, the pair (ia, ib[c]): one atomic
+// per warp, positions by an inclusive warp scan of the per-lane counts.
+__device__ __forceinline__ void emit_mask(const CheckArgs& a, uint32_t mask,
+                                          uint32_t ia, const uint32_t* ib,
+                                          int lane) {
+  uint32_t cnt = __popc(mask), incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) return;
   unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(a.count, (unsigned long long)__popc(bal));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (pass) {
-    unsigned long long slot = base + __popc(bal & ((1u << lane) - 1u));
-    if (slot < (unsigned long long)a.cap) {
-      uint32_t lo = i < j ? i : j, hi = i < j ? j : i;
-      a.cand[slot] = ((uint64_t)lo << 32) | hi;
+  if (lane == 31) base = atomicAdd(a.count, (unsigned long long)total);
+  base = __shfl_sync(0xffffffffu, base, 31) + (incl - cnt);
+  while (mask) {
+    const int c = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const uint32_t j = ib[c];
+    if (base < (unsigned long long)a.cap) {
+      const uint32_t lo = ia < j ? ia : j, hi = ia < j ? j : ia;
+      a.cand[base] = ((uint64_t)lo << 32) | hi;
     }
+    ++base;
   }
 }
 
@@ -252,6 +271,7 @@ check_kernel(CheckArgs a) {
   __shared__ uint64_t sm_s[kThreads / 32][32][W];
   __shared__ uint32_t sm_i[kThreads / 32][32];
   __shared__ uint64_t bm[kMaxBlocks][W];
+  __shared__ uint64_t sm_gm[kThreads / 32][kMaxBlocks][W];  // gap block masks
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < kMaxBlocks * W; t += kThreads)
     bm[t / W][t % W] = a.layout->mask[t / W][t % W];
@@ -273,17 +293,32 @@ check_kernel(CheckArgs a) {
   }
   uint32_t g = lo;
   const uint64_t* pool = a.strings + (size_t)a.q * a.n * W;
-  const unsigned lt = (1u << lane) - 1u;
-  (void)lt;
+  int cur_seg = -1, ngap = 0;
+  bool hashed = false;
+  uint64_t keep[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) keep[w] = 0;
   for (uint64_t item = w0; item < w1; ++item) {
     while (g + 1 < G && a.work_prefix[g + 1] <= item) ++g;
     const uint64_t local = item - a.work_prefix[g];
     const uint32_t st = a.starts[g];
     const uint32_t len = a.ends[g] - st + 1;
     const int seg = (int)(st / a.n);
-    const MaskDesc& md = a.masks[seg];
-    const uint32_t K = md.K;
-    const int maxK = md.maxK;
+    if (seg != cur_seg) {  // this grouping's first-mask test data
+      const MaskDesc& md = a.masks[seg];
+      cur_seg = seg;
+      ngap = md.ngap;
+      hashed = md.kept_bits > a.group_bits;
+#pragma unroll
+      for (int w = 0; w < W; ++w) keep[w] = md.keep[w];
+      __syncwarp();
+      if (lane < ngap) {
+        const int b = md.gap[lane];
+#pragma unroll
+        for (int w = 0; w < W; ++w) sm_gm[warp][lane][w] = bm[b][w];
+      }
+      __syncwarp();
+    }
     if (len <= kSmall) {
       if (lane < (int)len) {
         uint32_t idx = a.vals[st + lane];
@@ -292,23 +327,24 @@ check_kernel(CheckArgs a) {
         for (int w = 0; w < W; ++w) sm_s[warp][lane][w] = pool[(size_t)idx * W + w];
       }
       __syncwarp();
+      // pairs enumerated column by column: p = b(b-1)/2 + a, a < b
       const int P = (int)(len * (len - 1) / 2);
       for (int r = 0; r < P; r += 32) {
-        int p = r + lane;
+        const int p = r + lane;
         bool pass = false;
         uint32_t ii = 0, jj = 0;
         if (p < P) {
-          // pairs enumerated column by column: p = b(b-1)/2 + a, a < b
           int b = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
           while (b * (b - 1) / 2 > p) --b;
           while ((b + 1) * b / 2 <= p) ++b;
-          int aa = p - b * (b - 1) / 2;
+          const int aa = p - b * (b - 1) / 2;
           ii = sm_i[warp][aa];
           jj = sm_i[warp][b];
-          uint32_t i0 = ii < jj ? ii : jj, j0 = ii < jj ? jj : ii;
-          pass = pair_ok<W>(a, bm, K, maxK, i0, j0, sm_s[warp][aa], sm_s[warp][b]);
+          const uint32_t i0 = ii < jj ? ii : jj, j0 = ii < jj ? jj : ii;
+          pass = pair_ok<W>(a, sm_gm[warp], ngap, keep, hashed, i0, j0,
+                            sm_s[warp][aa], sm_s[warp][b]);
         }
-        emit(a, pass, ii, jj, lane);
+        emit_mask(a, pass ? 1u : 0u, ii, &jj, lane);
       }
       __syncwarp();
     } else {
@@ -338,18 +374,17 @@ check_kernel(CheckArgs a) {
       }
       __syncwarp();
       const bool diag = (I == J);
-      for (int c = 0; c < 32; ++c) {
-        uint32_t colpos = (uint32_t)(J * 32 + c);
-        bool v = va && colpos < len && (!diag || lane < c);
-        bool pass = false;
-        uint32_t ib = 0;
-        if (v) {
-          ib = sm_i[warp][c];
-          uint32_t i0 = ia < ib ? ia : ib, j0 = ia < ib ? ib : ia;
-          pass = pair_ok<W>(a, bm, K, maxK, i0, j0, sa, sm_s[warp][c]);
+      const uint32_t ncols = min(32u, len - (uint32_t)(J * 32));
+      uint32_t passm = 0;
+      if (va) {
+        for (uint32_t c = diag ? (uint32_t)lane + 1 : 0u; c < ncols; ++c) {
+          const uint32_t ib = sm_i[warp][c];
+          const uint32_t i0 = ia < ib ? ia : ib, j0 = ia < ib ? ib : ia;
+          if (pair_ok<W>(a, sm_gm[warp], ngap, keep, hashed, i0, j0, sa, sm_s[warp][c]))
+            passm |= 1u << c;
         }
-        emit(a, pass, ia, ib, lane);
       }
+      emit_mask(a, passm, ia, sm_i[warp], lane);
       __syncwarp();
     }
   }
@@ -413,6 +448,7 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   a.d = b.d;
   a.masks = b.masks;
   a.layout = b.layout;
+  a.group_bits = b.group_bits;
   a.cand = cand;
   a.cap = cap;
   a.count = count_dev;
