@@ -197,6 +197,28 @@ int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
                 uint64_t* pairs_out, float* dist_out, int64_t* count,
                 int64_t* recomputed, void* stream);
 
+/* msm_recheck for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a deployment variant.  It serves code that runs
+ * inside a host application owning the whole GPU (for example a serving
+ * process whose caching allocator has reserved the device, or a component
+ * held to a fixed memory budget), where a cudaMalloc issued from this
+ * library would fail or bypass the host's accounting.
+ *   Arguments, outputs and results are those of msm_recheck; the caller
+ *   still provides X, cand, pairs_out, dist_out and count.
+ *   Scratch: a static device array of about 3 MB per GPU that loads the
+ *   library (row norms and counters), so n must be <= 262144 (2^18) rows;
+ *   larger n returns MSM_E_INVAL with a message.  No cudaMalloc, cudaFree or
+ *   allocating library call is made.
+ *   The first call on each device looks up the array's device address (make
+ *   that first call before any stream capture).  Every call on a device uses
+ *   the same array and clears its counters first; calls whose work overlaps
+ *   on the GPU (other streams, other threads) race on it and must be
+ *   serialised by the caller.  Synchronises on `stream`. */
+int msm_recheck_noalloc(const void* X, int64_t n, int dim, int dtype,
+                        int metric, float eps, const uint64_t* cand, int64_t m,
+                        uint64_t* pairs_out, float* dist_out, int64_t* count,
+                        int64_t* recomputed, void* stream);
+
 /* The whole method (Sec. 4.1): projection, blockwise MSM over Q replicates
  * with replicate de-duplication, epsilon recheck.
  *   X          host or device [n][dim] of `dtype` (host memory is copied in)

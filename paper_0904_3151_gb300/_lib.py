@@ -73,6 +73,9 @@ SIGNATURES = {
                                      ctypes.POINTER(Pairs), ctypes.POINTER(Stats), vp]),
     "msm_recheck": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_float, vp, ctypes.c_int64, vp, vp, i64p, i64p, vp]),
+    "msm_recheck_noalloc": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_float, vp, ctypes.c_int64, vp,
+                                           vp, i64p, i64p, vp]),
     "msm_eps_graph": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_float, ctypes.c_double, ctypes.POINTER(Params),
                                      ctypes.POINTER(Allocator), ctypes.POINTER(Pairs),
