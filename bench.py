@@ -33,8 +33,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--Q", type=int, default=11)
+    # Q = 12: the smallest replicate count whose measured missing-edge ratio
+    # on this workload is <= 1e-6 (Q = 11 measured 1.03e-6)
+    ap.add_argument("--Q", type=int, default=12)
     ap.add_argument("--n", type=int, default=0, help="override n (0 = workload's)")
+    ap.add_argument("--clusters", type=int, default=0,
+                    help="override the number of clusters (0 = workload's)")
     ap.add_argument("--cpu-sample", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-missing", action="store_true")
@@ -190,6 +194,9 @@ def run_reference(a, wl, Q):
 def main():
     a = parse()
     wl = W.WORKLOADS["scale"]
+    if a.clusters:
+        import dataclasses
+        wl = dataclasses.replace(wl, n_clusters=a.clusters)
     Q = a.Q
     if a.impl == "reference":
         return run_reference(a, wl, Q)
@@ -316,17 +323,20 @@ def main():
     elif dom == "pair_check":
         # integer-ALU bound: pair inspections per second against the
         # issue-rate ceiling derived in the design notes
+        # unit: one pair inside a group; algorithmic work per pair in the
+        # field layout = 3 integer ops per 32-bit word of fields (xor, add,
+        # lop3) x ceil(k/2) words + 1 compare
         checks = st["checks"]
         avg_ms = kms[dom] / klaunch[dom]
         per_launch = checks / max(1, klaunch[dom] // a.steps)
         ach = per_launch / (avg_ms / 1000.0) / 1e9
-        ops_per_check = 12
+        ops_per_check = 3 * ((wl.k + 1) // 2) + 1
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
         peak = sm_count * 128 * peaks["sm_max_mhz"] * 1e6 / ops_per_check / 1e9
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak,
-                "unit": "Gchecks/s", "frac": ach / peak, "traffic": traffic_for(dom, "scale"),
-                "peak_source": f"derived: {sm_count} SMs x 128 int lanes x {peaks['sm_max_mhz']:.0f} MHz"
-                               f" / {ops_per_check} ops per check"}
+                "unit": "Gpairs/s", "frac": ach / peak, "traffic": traffic_for(dom, "scale"),
+                "peak_source": f"derived: {sm_count} SMs x 128 int32 lanes x "
+                               f"{peaks['sm_max_mhz']:.0f} MHz / {ops_per_check} ops per in-group pair"}
     elif dom == "project":
         flops = 2.0 * n * wl.dim * Q * wl.ell
         avg_ms = kms[dom] / klaunch[dom]

@@ -115,6 +115,12 @@ typedef struct msm_params {
   int group_bits;    /* grouping-key width 8..32; 0 = automatic         */
   int reserved;
   int64_t cand_capacity; /* initial candidate buffer (pairs); 0 = auto */
+  /* Optional projection features (learned form): when Y is non-NULL the
+   * strings are the sign projection of Y (device [n][dim_y] of dtype_y)
+   * instead of X, and R is [Q][dim_y][ell]; the recheck still uses X. */
+  const void* Y;
+  int dim_y;
+  int dtype_y;
 } msm_params;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -233,6 +239,44 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
                   float eps, double miss_ratio, const msm_params* params,
                   const msm_allocator* alloc, msm_pairs* out,
                   msm_stats* stats, void* stream);
+
+/* ---- Learned projection ----
+ * Sec. 6 of the paper proposes combining MSM with non-random hashing.  The
+ * learned form feeds the sign projection (Eq. 3) with features
+ *   y = W2 gelu(W1 x + b1) + b2      (gelu(h) = h Phi(h), exact erf form)
+ * instead of x (msm_params.Y); the epsilon recheck still uses x, so the
+ * result never contains a false pair.  Weights W1 [hidden][dim] and
+ * W2 [dim_out][hidden] are bf16 (raw 16-bit storage); biases, features and
+ * gradients are float; every product accumulates in float.
+ * Parameter vector order (float): W1, b1, W2, b2. */
+
+/* y for every row of X (device [n][dim] of dtype) into device Y
+ * [n][dim_out].  Scratch from cudaMallocAsync.  Asynchronous. */
+int msm_mlp_forward(const void* X, int64_t n, int dim, int dtype,
+                    const void* W1, const float* b1, const void* W2,
+                    const float* b2, int hidden, int dim_out, float* Y,
+                    void* stream);
+
+/* Training loss of `batch` pairs (pair_i[t], pair_j[t]) with label[t] = 1
+ * for an epsilon-neighbour pair and 0 otherwise:
+ *   mean of max(0, m_pos - cos(y_i, y_j)) (label 1), max(0, cos - m_neg)
+ * and its gradient with respect to (W1, b1, W2, b2), written to device
+ * `grads` (hidden*dim + hidden + dim_out*hidden + dim_out floats).
+ * *loss (host) receives the loss; synchronises. */
+int msm_mlp_grad(const void* X, int64_t n, int dim, int dtype, const void* W1,
+                 const float* b1, const void* W2, const float* b2, int hidden,
+                 int dim_out, const uint32_t* pair_i, const uint32_t* pair_j,
+                 const uint8_t* label, int64_t batch, float m_pos, float m_neg,
+                 float* grads, float* loss, void* stream);
+
+/* One Adam step (Kingma and Ba, 2015; step counts from 1) on the float
+ * master parameters `params` (device, the order above, `count` floats) with
+ * moment buffers m, v, then refresh of the bf16 copies W1_bf16, W2_bf16.
+ * Asynchronous. */
+int msm_mlp_adam(float* params, const float* grads, float* m, float* v,
+                 int64_t count, int step, float lr, float beta1, float beta2,
+                 float eps, void* W1_bf16, void* W2_bf16, int hidden, int dim,
+                 int dim_out, void* stream);
 
 /* Release the buffers of a msm_pairs returned by this library. */
 void msm_free_pairs(msm_pairs* p, const msm_allocator* alloc, void* stream);

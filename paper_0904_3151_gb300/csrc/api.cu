@@ -263,14 +263,34 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
                    PhaseTimer& tm) {
   cudaStream_t s = sc.stream();
   const BlockLayout L = make_layout(ell, k);
-  const std::vector<MaskDesc> masks = make_masks(L, d);
+  std::vector<MaskDesc> masks = make_masks(L, d);
   const int M = (int)masks.size();
-  int maxkept = 0;
-  for (const auto& m : masks) maxkept = m.kept_bits > maxkept ? m.kept_bits : maxkept;
+  int maxkept = 0, maxwidth = 0, anygap = 0;
+  for (const auto& m : masks) {
+    maxkept = m.kept_bits > maxkept ? m.kept_bits : maxkept;
+    anygap |= m.ngap > 0;
+  }
+  for (int b = 0; b < k; ++b) maxwidth = L.width[b] > maxwidth ? L.width[b] : maxwidth;
+  // Grouping key.  Automatic choice: when some grouping has gap blocks (and
+  // blocks are at most 16 bits) a 32-bit key = K-block part | first gap
+  // block, the K-block part exact if it fits, else the top bits of a 64-bit
+  // mix; otherwise the K blocks alone -- exact when they fit 24 bits, else
+  // a 24-bit mix (3 radix passes) while n <= 2^23, beyond that 32 bits.
+  // A mixed key lets unequal K blocks share a key for ~n^2 / 2^(bits+1)
+  // pairs per grouping; the in-group test rejects those pairs.
   int gb = group_bits_req;
-  if (gb <= 0) gb = maxkept <= 32 ? ((maxkept + 7) / 8) * 8 : 32;
+  const bool use_sub = gb <= 0 && anygap && maxwidth <= 16;
+  if (gb <= 0) {
+    if (use_sub) gb = 32;
+    else gb = maxkept <= 24 ? ((maxkept + 7) / 8) * 8 : (n <= (1ll << 23) ? 24 : 32);
+  }
   if (gb < 8) gb = 8;
   if (gb > 32) return set_error("group_bits must be <= 32"), MSM_E_INVAL;
+  for (auto& m : masks) {
+    m.sub_width = (use_sub && m.ngap > 0) ? L.width[m.gap[0]] : 0;
+    m.sub_lo = m.sub_width ? L.lo[m.gap[0]] : 0;
+    m.hashed = m.kept_bits > gb - m.sub_width;
+  }
   const int passes = (gb + 7) / 8;
   const int W = L.W;
 
@@ -290,6 +310,16 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
   MSM_CUDA(cudaMemsetAsync(counters, 0, 256, s));
   unsigned long long* count_dev = counters;
   unsigned long long* checks_dev = counters + 1;
+
+  // Field layout of every pool for the in-group checks, when the blocks fit.
+  const int FP = field_words(ell, k);
+  uint32_t* fields = nullptr;
+  if (FP > 0) {
+    fields = (uint32_t*)sc.get(4 * (size_t)Q * n * FP);
+    if (!fields) return MSM_E_NOMEM;
+    int rc = launch_fields(strings, (int64_t)Q * n, ell, k, fields, s);
+    if (rc) return rc;
+  }
 
   int64_t cap = cap0 > 0 ? cap0 : 16 * n;
   uint64_t* cand = (uint64_t*)sc.get(8 * (size_t)cap);
@@ -325,6 +355,9 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
       pb.group_bits = gb;
       pb.masks = dM + m0;
       pb.layout = dL;
+      pb.fields = fields;
+      pb.FP = FP;
+      pb.FU = (k + 1) / 2;
       tm.mark(3);
       rc = find_groups(pb, pws, checks_dev, s);
       if (rc) return rc;
@@ -601,7 +634,7 @@ int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
   unsigned long long* ctr = (unsigned long long*)sc.get(256);
   if (!ctr) return MSM_E_NOMEM;
   MSM_CUDA(cudaMemsetAsync(ctr, 0, 256, s));
-  rc = launch_recheck(X, dtype, n, dim, metric, eps, n64, cand, nullptr, m,
+  rc = launch_recheck(X, dtype, n, dim, metric, eps, n32, cand, nullptr, m,
                       pairs_out, dist_out, ctr, ctr + 1, s);
   if (rc) return rc;
   unsigned long long h[2] = {0, 0};
@@ -653,11 +686,28 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
   float* n32;
   rc = norms_and_check(sc, Xd, dtype, n, dim, metric, &n64, &n32);
   if (rc) return rc;
+  // Projection input: X itself, or the learned features Y.
+  const void* P = Xd;
+  int pdim = dim, pdtype = dtype;
+  const float* pnorm = n32;
+  if (params->Y) {
+    P = params->Y;
+    pdim = params->dim_y;
+    pdtype = params->dtype_y;
+    if (pdim < 1 || pdim > kMaxDim || (pdtype != MSM_DT_F32 && pdtype != MSM_DT_BF16) ||
+        !is_device_ptr(P))
+      return set_error("msm_params.Y must be device [n][dim_y] float or bf16"), MSM_E_INVAL;
+    double* y64;
+    float* y32;
+    rc = norms_and_check(sc, P, pdtype, n, pdim, MSM_EUCLIDEAN, &y64, &y32);
+    if (rc) return rc;
+    pnorm = y32;
+  }
   const float* R = params->R;
   if (!R) {
-    float* g = (float*)sc.get(4 * (size_t)Q * dim * ell);
+    float* g = (float*)sc.get(4 * (size_t)Q * pdim * ell);
     if (!g) return MSM_E_NOMEM;
-    rc = launch_gaussian(params->seed, (int64_t)Q * dim * ell, g, s);
+    rc = launch_gaussian(params->seed, (int64_t)Q * pdim * ell, g, s);
     if (rc) return rc;
     R = g;
   }
@@ -667,7 +717,7 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
   if (!strings || !ctr) return MSM_E_NOMEM;
   MSM_CUDA(cudaMemsetAsync(ctr, 0, 256, s));
   tm.mark(1);
-  rc = run_projection(sc, Xd, dtype, n, dim, R, n32, Q, ell, params->flags,
+  rc = run_projection(sc, P, pdtype, n, pdim, R, pnorm, Q, ell, params->flags,
                       strings, ctr + 2);
   if (rc) return rc;
 
@@ -691,7 +741,7 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
     }
   }
   tm.mark(5);
-  rc = launch_recheck(Xd, dtype, n, dim, metric, eps, n64, cand, nullptr, m,
+  rc = launch_recheck(Xd, dtype, n, dim, metric, eps, n32, cand, nullptr, m,
                       pairs, dist, ctr, ctr + 1, s);
   if (rc) return rc;
   unsigned long long h[3] = {0, 0, 0};
@@ -723,6 +773,57 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
   return MSM_OK;
 }
 
+int msm_mlp_forward(const void* X, int64_t n, int dim, int dtype, const void* W1,
+                    const float* b1, const void* W2, const float* b2, int hidden,
+                    int dim_out, float* Y, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!X || !W1 || !b1 || !W2 || !b2 || !Y || n < 1 || dim < 1 || hidden < 1 ||
+      dim_out < 1 || (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16))
+    return set_error("invalid msm_mlp_forward arguments"), MSM_E_INVAL;
+  Scratch sc(nullptr, s);
+  const int64_t chunk = n < (1 << 18) ? n : (1 << 18);
+  float* H = (float*)sc.get(4 * (size_t)chunk * hidden);
+  float* A = (float*)sc.get(4 * (size_t)chunk * hidden);
+  if (!H || !A) return MSM_E_NOMEM;
+  return mlp_forward(X, dtype, n, dim, W1, b1, W2, b2, hidden, dim_out, Y, H, A, chunk, nullptr,
+                     s);
+}
+
+int msm_mlp_grad(const void* X, int64_t n, int dim, int dtype, const void* W1,
+                 const float* b1, const void* W2, const float* b2, int hidden,
+                 int dim_out, const uint32_t* pair_i, const uint32_t* pair_j,
+                 const uint8_t* label, int64_t batch, float m_pos, float m_neg,
+                 float* grads, float* loss, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!X || !W1 || !b1 || !W2 || !b2 || !pair_i || !pair_j || !label || !grads ||
+      batch < 1 || batch > (1 << 24) || n < 2 || dim < 1 || hidden < 1 || dim_out < 1 ||
+      (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16))
+    return set_error("invalid msm_mlp_grad arguments"), MSM_E_INVAL;
+  Scratch sc(nullptr, s);
+  const int64_t P = 2 * batch;
+  void* ws = sc.get(4 * (size_t)P * (2 * hidden + 2 * dim_out) + 4 * (size_t)P + 256);
+  float* ld = (float*)sc.get(256);
+  if (!ws || !ld) return MSM_E_NOMEM;
+  int rc = mlp_grad(X, dtype, n, dim, W1, b1, W2, b2, hidden, dim_out, pair_i, pair_j, label,
+                    batch, m_pos, m_neg, grads, ld, ws, s);
+  if (rc) return rc;
+  float h = 0.f;
+  rc = read_back(&h, ld, s);
+  if (rc) return rc;
+  if (loss) *loss = h;
+  return MSM_OK;
+}
+
+int msm_mlp_adam(float* params, const float* grads, float* m, float* v, int64_t count,
+                 int step, float lr, float beta1, float beta2, float eps, void* W1_bf16,
+                 void* W2_bf16, int hidden, int dim, int dim_out, void* stream) {
+  if (!params || !grads || !m || !v || !W1_bf16 || !W2_bf16 || step < 1 ||
+      count != (int64_t)hidden * dim + hidden + (int64_t)dim_out * hidden + dim_out)
+    return set_error("invalid msm_mlp_adam arguments"), MSM_E_INVAL;
+  return mlp_adam(params, grads, m, v, count, step, lr, beta1, beta2, eps, W1_bf16, W2_bf16,
+                  hidden, dim, dim_out, (cudaStream_t)stream);
+}
+
 void msm_free_pairs(msm_pairs* p, const msm_allocator* alloc, void* stream) {
   if (!p) return;
   raw_free(alloc, p->pairs, (cudaStream_t)stream);
@@ -748,7 +849,7 @@ int msm_eps_count_exhaustive(const void* X, int64_t n, int dim, int dtype,
   unsigned long long* ctr = (unsigned long long*)sc.get(256);
   if (!ctr) return MSM_E_NOMEM;
   MSM_CUDA(cudaMemsetAsync(ctr, 0, 256, s));
-  rc = launch_eps_count(X, dtype, n, dim, metric, eps, n64, ctr, s);
+  rc = launch_eps_count(X, dtype, n, dim, metric, eps, n32, ctr, s);
   if (rc) return rc;
   unsigned long long c = 0;
   rc = read_back(&c, ctr, s);

@@ -43,6 +43,8 @@ __device__ __forceinline__ uint64_t extract_bits(const uint64_t* s, int lo,
 struct KeptList {
   int n;
   int exact;
+  int kbits;              // bits of the K-block part of the key
+  int sub_lo, sub_width;  // first gap block appended below the K part
   int lo[kMaxBlocks];
   int width[kMaxBlocks];
   uint64_t keep[kMaxWords];
@@ -60,7 +62,10 @@ __device__ void setup_kept(KeptList& kl, const MaskDesc& md,
         ++c;
       }
     kl.n = c;
-    kl.exact = md.kept_bits <= group_bits;
+    kl.exact = !md.hashed;
+    kl.kbits = group_bits - md.sub_width;
+    kl.sub_lo = md.sub_lo;
+    kl.sub_width = md.sub_width;
     for (int w = 0; w < kMaxWords; ++w) kl.keep[w] = md.keep[w];
   }
 }
@@ -71,20 +76,23 @@ __device__ __forceinline__ uint32_t group_key(const uint64_t* str, int W,
   uint64_t s[kMaxWords];
 #pragma unroll
   for (int w = 0; w < kMaxWords; ++w) s[w] = w < W ? str[w] : 0;
+  uint64_t kpart;
   if (kl.exact) {
-    uint64_t key = 0;
+    kpart = 0;
     int off = 0;
     for (int c = 0; c < kl.n; ++c) {
-      key |= extract_bits(s, kl.lo[c], kl.width[c]) << off;
+      kpart |= extract_bits(s, kl.lo[c], kl.width[c]) << off;
       off += kl.width[c];
     }
-    return (uint32_t)key;
-  }
-  uint64_t h = 0x9E3779B97F4A7C15ull;
+  } else {
+    uint64_t h = 0x9E3779B97F4A7C15ull;
 #pragma unroll
-  for (int w = 0; w < kMaxWords; ++w)
-    if (w < W) h = fmix64(h ^ (s[w] & kl.keep[w]));
-  return (uint32_t)(h >> (64 - group_bits));
+    for (int w = 0; w < kMaxWords; ++w)
+      if (w < W) h = fmix64(h ^ (s[w] & kl.keep[w]));
+    kpart = h >> (64 - kl.kbits);
+  }
+  if (kl.sub_width == 0) return (uint32_t)kpart;
+  return (uint32_t)((kpart << kl.sub_width) | extract_bits(s, kl.sub_lo, kl.sub_width));
 }
 
 struct SortArgs {

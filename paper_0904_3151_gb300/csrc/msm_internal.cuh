@@ -33,6 +33,11 @@ struct MaskDesc {
   int ngap;                  // blocks below maxK that are not kept
   uint8_t gap[kMaxBlocks];   // those blocks: a pair is reported under K only
                              // if it differs in every one of them
+  // Grouping key = (K-block part << sub_width) | value of the first gap
+  // block.  Strings equal on that block can never be reported under K, so
+  // runs of equal full keys inside a group need no inspection.
+  int sub_lo, sub_width;     // first gap block (width 0: no sub-key)
+  int hashed;                // K-block part is a mix, not the exact blocks
 };
 
 // ---------------------------------------------------------------- errors
@@ -168,8 +173,16 @@ struct PairBatch {
                              // kept bits fit)
   const MaskDesc* masks;     // device [S]
   const BlockLayout* layout; // device copy
+  const uint32_t* fields;    // optional field layout [Q][n][FP] (or NULL)
+  int FP;                    // stored words per string (even)
+  int FU;                    // words holding fields, ceil(k / 2)
 };
 size_t pairs_scratch_bytes(int64_t items);
+// Field layout: every block in its own 16-bit field, FP (even) words per
+// string; field_words returns 0 when a block exceeds 15 bits or k > 16.
+int field_words(int ell, int k);
+int launch_fields(const uint64_t* strings, int64_t count, int ell, int k,
+                  uint32_t* fields, cudaStream_t s);
 // Finds the groups of >= 2 equal keys; returns on the device the number
 // of work items and adds sum C(size,2) to *checks_dev.
 int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
@@ -179,15 +192,29 @@ int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
 int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
                  unsigned long long* count_dev, cudaStream_t s);
 
+// mlp.cu: learned projection network
+int mlp_forward(const void* X, int dtype, int64_t n, int dim, const void* W1,
+                const float* b1, const void* W2, const float* b2, int hidden,
+                int dim_out, float* Y, float* Hbuf, float* Abuf, int64_t chunk,
+                const uint32_t* rowmap, cudaStream_t s);
+int mlp_grad(const void* X, int dtype, int64_t n, int dim, const void* W1,
+             const float* b1, const void* W2, const float* b2, int hidden, int dim_out,
+             const uint32_t* pi, const uint32_t* pj, const uint8_t* label, int64_t B,
+             float m_pos, float m_neg, float* grads, float* loss_dev, void* ws,
+             cudaStream_t s);
+int mlp_adam(float* params, const float* grads, float* m, float* v, int64_t count,
+             int step, float lr, float beta1, float beta2, float eps, void* w1h, void* w2h,
+             int hidden, int dim, int dim_out, cudaStream_t s);
+
 // recheck.cu
 int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
-                   float eps, const double* nrm64, const uint64_t* cand,
+                   float eps, const float* nrm32, const uint64_t* cand,
                    const unsigned long long* m_dev, int64_t m_max,
                    uint64_t* pairs_out, float* dist_out,
                    unsigned long long* count_dev,
                    unsigned long long* recompute_dev, cudaStream_t s);
 int launch_eps_count(const void* X, int dtype, int64_t n, int dim, int metric,
-                     float eps, const double* nrm64,
+                     float eps, const float* nrm32,
                      unsigned long long* count_dev, cudaStream_t s);
 
 }  // namespace msm

@@ -34,8 +34,10 @@ struct GroupWs {
   uint32_t* ends;         // [items/2 + 1]
   uint64_t* work;         // [items/2 + 1]
   uint64_t* work_prefix;  // [items/2 + 1]
+  uint32_t* chunk_group;  // [items/2 + 1]: group holding each chunk's first item
   uint32_t* ngroups;      // [1]
   uint64_t* total_work;   // [1]
+  unsigned* grab;         // [1]: next chunk to hand out
   void* scan_ws;
 };
 
@@ -52,35 +54,74 @@ GroupWs carve(void* ws, int64_t items) {
   g.ends = reinterpret_cast<uint32_t*>(p); p += align256(4 * (size_t)maxg);
   g.work = reinterpret_cast<uint64_t*>(p); p += align256(8 * (size_t)maxg);
   g.work_prefix = reinterpret_cast<uint64_t*>(p); p += align256(8 * (size_t)maxg);
+  g.chunk_group = reinterpret_cast<uint32_t*>(p); p += align256(4 * (size_t)maxg);
   g.ngroups = reinterpret_cast<uint32_t*>(p); p += 256;
   g.total_work = reinterpret_cast<uint64_t*>(p); p += 256;
+  g.grab = reinterpret_cast<unsigned*>(p); p += 256;
   g.scan_ws = p;
   return g;
 }
 
+// Work items are handed out in chunks of `chunk_size(total, cap)` items
+// (at least 32, and few enough chunks to index `cap` of them).
+__host__ __device__ __forceinline__ uint64_t chunk_size(uint64_t total, uint64_t cap) {
+  const uint64_t c = (total + cap - 1) / cap;
+  return c < 32 ? 32 : c;
+}
+
+// chunk_group[c] = the group containing work item c * chunk_size.
+__global__ void chunk_index_kernel(const uint64_t* work_prefix,
+                                   const uint32_t* ngroups,
+                                   const uint64_t* total_work, uint64_t cap,
+                                   uint32_t* chunk_group) {
+  const uint64_t total = *total_work;
+  const uint32_t G = *ngroups;
+  if (total == 0 || G == 0) return;
+  const uint64_t C = chunk_size(total, cap);
+  const uint64_t nch = (total + C - 1) / C;
+  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < nch;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t item = c * C;
+    uint32_t lo = 0, hi = G - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (work_prefix[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    chunk_group[c] = lo;
+  }
+}
+
 // Run boundary flags of flat position p whose offset in its segment (of
-// length n) is `local`.
+// length n) is `local`; runs are equal K-block parts of the key (the key
+// shifted right by the segment's sub-key width sw).
 __device__ __forceinline__ void run_flags(const uint32_t* keys, int64_t n,
-                                          int64_t p, int64_t local,
+                                          int64_t p, int64_t local, int sw,
                                           bool& start, bool& end) {
-  uint32_t k = keys[p];
-  bool head = (local == 0) || keys[p - 1] != k;
-  bool tail = (local == n - 1) || keys[p + 1] != k;
+  uint32_t k = keys[p] >> sw;
+  bool head = (local == 0) || (keys[p - 1] >> sw) != k;
+  bool tail = (local == n - 1) || (keys[p + 1] >> sw) != k;
   start = head && !tail;
   end = tail && !head;
 }
 
 __global__ void run_count_kernel(const uint32_t* keys, int64_t items, int64_t n,
-                                 uint32_t* cnt_start, uint32_t* cnt_end) {
+                                 const MaskDesc* masks, uint32_t* cnt_start,
+                                 uint32_t* cnt_end) {
   int64_t p0 = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * 16;
   uint32_t cs = 0, ce = 0;
   int64_t local = p0 % n;
+  int64_t seg = p0 / n;
+  int sw = p0 < items ? masks[seg].sub_width : 0;
   for (int j = 0; j < 16; ++j, ++local) {
-    if (local >= n) local -= n;
+    if (local >= n) {
+      local -= n;
+      ++seg;
+      if (p0 + j < items) sw = masks[seg].sub_width;
+    }
     int64_t p = p0 + j;
     if (p < items) {
       bool s, e;
-      run_flags(keys, n, p, local, s, e);
+      run_flags(keys, n, p, local, sw, s, e);
       cs += s;
       ce += e;
     }
@@ -126,6 +167,7 @@ __device__ __forceinline__ uint32_t block_excl(uint32_t v, uint32_t* tmp,
 }
 
 __global__ void run_write_kernel(const uint32_t* keys, int64_t items, int64_t n,
+                                 const MaskDesc* masks,
                                  const uint32_t* off_start,
                                  const uint32_t* off_end, uint32_t* starts,
                                  uint32_t* ends, int64_t nchunks,
@@ -134,12 +176,18 @@ __global__ void run_write_kernel(const uint32_t* keys, int64_t items, int64_t n,
   int64_t p0 = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * 16;
   uint32_t fs = 0, fe = 0;  // bit j: start / end at p0 + j
   int64_t local = p0 % n;
+  int64_t seg = p0 / n;
+  int sw = p0 < items ? masks[seg].sub_width : 0;
   for (int j = 0; j < 16; ++j, ++local) {
-    if (local >= n) local -= n;
+    if (local >= n) {
+      local -= n;
+      ++seg;
+      if (p0 + j < items) sw = masks[seg].sub_width;
+    }
     int64_t p = p0 + j;
     if (p < items) {
       bool s, e;
-      run_flags(keys, n, p, local, s, e);
+      run_flags(keys, n, p, local, sw, s, e);
       fs |= (uint32_t)s << j;
       fe |= (uint32_t)e << j;
     }
@@ -177,6 +225,10 @@ __global__ void run_work_kernel(const uint32_t* starts, const uint32_t* ends,
 
 // ------------------------------------------------------------ pair check
 struct CheckArgs {
+  const uint32_t* keys;     // sorted grouping keys (sub-group test)
+  const uint32_t* chunk_group;
+  unsigned* grab;
+  uint64_t chunk_cap;
   const uint32_t* vals;
   const uint32_t* starts;
   const uint32_t* ends;
@@ -196,27 +248,35 @@ struct CheckArgs {
   unsigned long long* count;
 };
 
-// The three tests of one pair, cheapest and most selective first.
-//   first-mask rule: K blocks equal (only in doubt when keys were hashed)
-//   and every gap block (below max K, not kept) different;
-//   Hamming <= d; no earlier replicate within d (Appendix).
+// The tests of one pair, most selective first:
+//   first-mask rule, part 1: every gap block (below max K, not kept)
+//   differs -- rejects almost every pair that is not reported here;
+//   Hamming <= d;
+//   first-mask rule, part 2: the K blocks are equal -- true for every
+//   grouped pair unless two different K-block values shared a hashed key;
+//   no earlier replicate within d (Appendix).
+constexpr int kRegGaps = 6;  // gap masks held in registers (ngap <= d)
+
 template <int W>
-__device__ __forceinline__ bool pair_ok(const CheckArgs& a,
-                                        const uint64_t (*gm)[W], int ngap,
-                                        const uint64_t* keep, bool hashed,
-                                        uint32_t i, uint32_t j,
-                                        const uint64_t* si,
-                                        const uint64_t* sj) {
+__device__ __forceinline__ bool strings_ok(const CheckArgs& a,
+                                           const uint64_t (*gm)[W], int ngap,
+                                           const uint64_t (&rg)[kRegGaps][W],
+                                           const uint64_t* keep, bool hashed,
+                                           const uint64_t* si,
+                                           const uint64_t* sj) {
   uint64_t x[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) x[w] = si[w] ^ sj[w];
-  if (hashed) {
-    uint64_t o = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) o |= x[w] & keep[w];
-    if (o) return false;
+  for (int gI = 0; gI < kRegGaps; ++gI) {
+    if (gI < ngap) {
+      uint64_t o = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w) o |= x[w] & rg[gI][w];
+      if (o == 0) return false;
+    }
   }
-  for (int gI = 0; gI < ngap; ++gI) {
+  for (int gI = kRegGaps; gI < ngap; ++gI) {
     uint64_t o = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) o |= x[w] & gm[gI][w];
@@ -226,6 +286,18 @@ __device__ __forceinline__ bool pair_ok(const CheckArgs& a,
 #pragma unroll
   for (int w = 0; w < W; ++w) h += __popcll(x[w]);
   if (h > a.d) return false;
+  if (hashed) {
+    uint64_t o = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) o |= x[w] & keep[w];
+    if (o) return false;
+  }
+  return true;
+}
+
+template <int W>
+__device__ __forceinline__ bool replicates_ok(const CheckArgs& a, uint32_t i,
+                                              uint32_t j) {
   for (int g = 0; g < a.q; ++g) {
     const uint64_t* gi = a.strings + ((size_t)g * a.n + i) * W;
     const uint64_t* gj = a.strings + ((size_t)g * a.n + j) * W;
@@ -279,25 +351,28 @@ check_kernel(CheckArgs a) {
   const uint64_t total = *a.total_work;
   const uint32_t G = *a.ngroups;
   if (total == 0 || G == 0) return;
-  const uint64_t nwarps = (uint64_t)gridDim.x * (kThreads / 32);
-  const uint64_t gw = (uint64_t)blockIdx.x * (kThreads / 32) + warp;
-  const uint64_t per = (total + nwarps - 1) / nwarps;
-  const uint64_t w0 = gw * per;
-  const uint64_t w1 = min(total, w0 + per);
-  if (w0 >= w1) return;
-  // group containing work item w0: last g with work_prefix[g] <= w0
-  uint32_t lo = 0, hi = G - 1;
-  while (lo < hi) {
-    uint32_t mid = (lo + hi + 1) >> 1;
-    if (a.work_prefix[mid] <= w0) lo = mid; else hi = mid - 1;
-  }
-  uint32_t g = lo;
+  const uint64_t C = chunk_size(total, a.chunk_cap);
+  const uint64_t nch = (total + C - 1) / C;
   const uint64_t* pool = a.strings + (size_t)a.q * a.n * W;
   int cur_seg = -1, ngap = 0;
   bool hashed = false;
   uint64_t keep[W];
+  uint64_t rg[kRegGaps][W];
 #pragma unroll
   for (int w = 0; w < W; ++w) keep[w] = 0;
+#pragma unroll
+  for (int gI = 0; gI < kRegGaps; ++gI)
+#pragma unroll
+    for (int w = 0; w < W; ++w) rg[gI][w] = 0;
+  // chunks of consecutive work items are handed out dynamically: items
+  // differ ~10x in cost, so static ranges leave most warps idle at the end
+  for (;;) {
+  unsigned chunk = 0;
+  if (lane == 0) chunk = atomicAdd(a.grab, 1u);
+  chunk = __shfl_sync(0xffffffffu, chunk, 0);
+  if (chunk >= nch) break;
+  const uint64_t w0 = (uint64_t)chunk * C, w1 = min(total, w0 + C);
+  uint32_t g = a.chunk_group[chunk];
   for (uint64_t item = w0; item < w1; ++item) {
     while (g + 1 < G && a.work_prefix[g + 1] <= item) ++g;
     const uint64_t local = item - a.work_prefix[g];
@@ -308,7 +383,7 @@ check_kernel(CheckArgs a) {
       const MaskDesc& md = a.masks[seg];
       cur_seg = seg;
       ngap = md.ngap;
-      hashed = md.kept_bits > a.group_bits;
+      hashed = md.hashed != 0;
 #pragma unroll
       for (int w = 0; w < W; ++w) keep[w] = md.keep[w];
       __syncwarp();
@@ -318,6 +393,10 @@ check_kernel(CheckArgs a) {
         for (int w = 0; w < W; ++w) sm_gm[warp][lane][w] = bm[b][w];
       }
       __syncwarp();
+#pragma unroll
+      for (int gI = 0; gI < kRegGaps; ++gI)
+#pragma unroll
+        for (int w = 0; w < W; ++w) rg[gI][w] = gI < ngap ? sm_gm[warp][gI][w] : 0;
     }
     if (len <= kSmall) {
       if (lane < (int)len) {
@@ -338,13 +417,23 @@ check_kernel(CheckArgs a) {
           while (b * (b - 1) / 2 > p) --b;
           while ((b + 1) * b / 2 <= p) ++b;
           const int aa = p - b * (b - 1) / 2;
-          ii = sm_i[warp][aa];
-          jj = sm_i[warp][b];
-          const uint32_t i0 = ii < jj ? ii : jj, j0 = ii < jj ? jj : ii;
-          pass = pair_ok<W>(a, sm_gm[warp], ngap, keep, hashed, i0, j0,
-                            sm_s[warp][aa], sm_s[warp][b]);
+          if (strings_ok<W>(a, sm_gm[warp], ngap, rg, keep, hashed, sm_s[warp][aa],
+                            sm_s[warp][b])) {
+            ii = sm_i[warp][aa];
+            jj = sm_i[warp][b];
+            const uint32_t i0 = ii < jj ? ii : jj, j0 = ii < jj ? jj : ii;
+            pass = replicates_ok<W>(a, i0, j0);
+          }
         }
-        emit_mask(a, pass ? 1u : 0u, ii, &jj, lane);
+        // one pair per lane: a ballot gives the positions
+        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+        if (bal) {
+          unsigned long long b0 = 0;
+          if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)__popc(bal));
+          b0 = __shfl_sync(0xffffffffu, b0, 0) + __popc(bal & ((1u << lane) - 1u));
+          if (pass && b0 < (unsigned long long)a.cap)
+            a.cand[b0] = ((uint64_t)(ii < jj ? ii : jj) << 32) | (ii < jj ? jj : ii);
+        }
       }
       __syncwarp();
     } else {
@@ -378,9 +467,272 @@ check_kernel(CheckArgs a) {
       uint32_t passm = 0;
       if (va) {
         for (uint32_t c = diag ? (uint32_t)lane + 1 : 0u; c < ncols; ++c) {
+          if (strings_ok<W>(a, sm_gm[warp], ngap, rg, keep, hashed, sa, sm_s[warp][c])) {
+            const uint32_t ib = sm_i[warp][c];
+            const uint32_t i0 = ia < ib ? ia : ib, j0 = ia < ib ? ib : ia;
+            if (replicates_ok<W>(a, i0, j0)) passm |= 1u << c;
+          }
+        }
+      }
+      emit_mask(a, passm, ia, sm_i[warp], lane);
+      __syncwarp();
+    }
+  }
+  }
+}
+
+// ------------------------------------------------- field-layout variant
+// Every block b of a string is re-packed into its own 16-bit field (word
+// b >> 1, bits 16 (b & 1) ...), guard bits zero.  For x = f_i ^ f_j the field
+// of a block is nonzero iff bit 15 of (field + 0x7FFF) is set; blocks of at
+// most 15 bits cannot carry into the next field, so one add and one mask
+// test two blocks per 32-bit word.  The gap test of the first-mask rule
+// ("every gap block differs") then costs 3 integer operations per word and
+// no branch, whatever the number of gap blocks, and Hamming distances are
+// unchanged (guard bits cancel in the xor).
+constexpr int kMaxFieldBlocks = 16;
+
+struct FieldLayout {
+  int k;
+  int lo[kMaxFieldBlocks];
+  int width[kMaxFieldBlocks];
+};
+
+template <int W>
+__device__ __forceinline__ uint64_t pick_word(const uint64_t (&s)[W], int i) {
+  uint64_t v = s[0];
+#pragma unroll
+  for (int w = 1; w < W; ++w) v = (i == w) ? s[w] : v;
+  return v;
+}
+
+template <int W, int FP>
+__global__ void fields_kernel(const uint64_t* strings, int64_t count,
+                              FieldLayout L, uint32_t* fields) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t s[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) s[w] = strings[t * W + w];
+    uint32_t f[FP];
+#pragma unroll
+    for (int w = 0; w < FP; ++w) f[w] = 0;
+#pragma unroll
+    for (int b = 0; b < kMaxFieldBlocks; ++b) {
+      if (b < L.k && (b >> 1) < FP) {
+        const int lo = L.lo[b], wd = L.width[b];
+        const int wi = lo >> 6, sh = lo & 63;
+        uint64_t v = pick_word<W>(s, wi) >> sh;
+        if (sh + wd > 64) v |= pick_word<W>(s, wi + 1) << (64 - sh);
+        f[b >> 1] |= (uint32_t)(v & ((1ull << wd) - 1)) << ((b & 1) * 16);
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < FP; w += 2)
+      *reinterpret_cast<uint2*>(fields + t * FP + w) = make_uint2(f[w], f[w + 1]);
+  }
+}
+
+// Gap test of one pair: true iff every gap field of x = a ^ b is nonzero.
+// FU = words that hold fields (the stored FP may include one padding word).
+template <int FP, int FU>
+__device__ __forceinline__ bool gaps_differ(const uint32_t (&fa)[FP],
+                                            const uint32_t* fb,
+                                            const uint32_t (&gapf)[FP]) {
+  uint32_t bad = 0;
+#pragma unroll
+  for (int w = 0; w < FU; ++w) {
+    const uint32_t x = fa[w] ^ fb[w];
+    const uint32_t nz = (x + 0x7FFF7FFFu) & 0x80008000u;
+    bad |= gapf[w] & ~nz;
+  }
+  return bad == 0;
+}
+
+// Hamming <= d and (hashed keys only) all kept fields equal.
+template <int FP, int FU>
+__device__ __forceinline__ bool fields_rest_ok(const uint32_t (&fa)[FP],
+                                               const uint32_t* fb, int d,
+                                               bool hashed,
+                                               const uint32_t (&keepf)[FP]) {
+  int h = 0;
+  uint32_t bad = 0;
+#pragma unroll
+  for (int w = 0; w < FU; ++w) {
+    const uint32_t x = fa[w] ^ fb[w];
+    h += __popc(x);
+    bad |= keepf[w] & ((x + 0x7FFF7FFFu) & 0x80008000u);
+  }
+  return h <= d && (!hashed || bad == 0);
+}
+
+template <int FP>
+__device__ __forceinline__ bool replicates_ok_fields(const CheckArgs& a,
+                                                     const uint32_t* fields,
+                                                     uint32_t i, uint32_t j) {
+  for (int g = 0; g < a.q; ++g) {
+    const uint2* fi = reinterpret_cast<const uint2*>(fields + ((size_t)g * a.n + i) * FP);
+    const uint2* fj = reinterpret_cast<const uint2*>(fields + ((size_t)g * a.n + j) * FP);
+    int h = 0;
+#pragma unroll
+    for (int w = 0; w < FP / 2; ++w) {
+      const uint2 p = __ldg(fi + w), q2 = __ldg(fj + w);
+      h += __popc(p.x ^ q2.x) + __popc(p.y ^ q2.y);
+    }
+    if (h <= a.d) return false;
+  }
+  return true;
+}
+
+template <int FP, int FU>
+__global__ void __launch_bounds__(kThreads)
+check_fields_kernel(CheckArgs a, const uint32_t* fields) {
+  __shared__ __align__(16) uint32_t sm_f[kThreads / 32][32][FP];
+  __shared__ uint32_t sm_i[kThreads / 32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t total = *a.total_work;
+  const uint32_t G = *a.ngroups;
+  if (total == 0 || G == 0) return;
+  const uint64_t C = chunk_size(total, a.chunk_cap);
+  const uint64_t nch = (total + C - 1) / C;
+  const uint32_t* pool = fields + (size_t)a.q * a.n * FP;
+  int cur_seg = -1, subw = 0;
+  bool hashed = false;
+  uint32_t gapf[FP], keepf[FP];
+#pragma unroll
+  for (int w = 0; w < FP; ++w) gapf[w] = keepf[w] = 0;
+  for (;;) {  // dynamic chunks of work items (see check_kernel)
+  unsigned chunk = 0;
+  if (lane == 0) chunk = atomicAdd(a.grab, 1u);
+  chunk = __shfl_sync(0xffffffffu, chunk, 0);
+  if (chunk >= nch) break;
+  const uint64_t w0 = (uint64_t)chunk * C, w1 = min(total, w0 + C);
+  uint32_t g = a.chunk_group[chunk];
+  for (uint64_t item = w0; item < w1; ++item) {
+    while (g + 1 < G && a.work_prefix[g + 1] <= item) ++g;
+    const uint64_t local = item - a.work_prefix[g];
+    const uint32_t st = a.starts[g];
+    const uint32_t len = a.ends[g] - st + 1;
+    const int seg = (int)(st / a.n);
+    if (seg != cur_seg) {
+      const MaskDesc& md = a.masks[seg];
+      cur_seg = seg;
+      hashed = md.hashed != 0;
+      subw = md.sub_width;
+      // gap blocks: below the highest kept block and not kept
+      const uint32_t K = md.K;
+      const uint32_t Gs = ((1u << md.maxK) - 1u) & ~K;
+#pragma unroll
+      for (int w = 0; w < FP; ++w) {
+        gapf[w] = ((Gs >> (2 * w)) & 1u ? 0x8000u : 0u) |
+                  ((Gs >> (2 * w + 1)) & 1u ? 0x80000000u : 0u);
+        keepf[w] = ((K >> (2 * w)) & 1u ? 0x8000u : 0u) |
+                   ((K >> (2 * w + 1)) & 1u ? 0x80000000u : 0u);
+      }
+    }
+    if (len <= kSmall) {
+      // all members equal on the first gap block: nothing to report here
+      if (subw && a.keys[st] == a.keys[st + len - 1]) continue;
+      if (lane < (int)len) {
+        const uint32_t idx = a.vals[st + lane];
+        sm_i[warp][lane] = idx;
+        const uint2* src = reinterpret_cast<const uint2*>(pool + (size_t)idx * FP);
+#pragma unroll
+        for (int w = 0; w < FP; w += 2) {
+          const uint2 v = src[w / 2];
+          sm_f[warp][lane][w] = v.x;
+          sm_f[warp][lane][w + 1] = v.y;
+        }
+      }
+      __syncwarp();
+      const int P = (int)(len * (len - 1) / 2);
+      for (int r = 0; r < P; r += 32) {
+        const int p = r + lane;
+        bool pass = false;
+        uint32_t ii = 0, jj = 0;
+        if (p < P) {
+          int b = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
+          while (b * (b - 1) / 2 > p) --b;
+          while ((b + 1) * b / 2 <= p) ++b;
+          const int aa = p - b * (b - 1) / 2;
+          uint32_t fa[FP];
+#pragma unroll
+          for (int w = 0; w < FP; ++w) fa[w] = sm_f[warp][aa][w];
+          if (gaps_differ<FP, FU>(fa, sm_f[warp][b], gapf) &&
+              fields_rest_ok<FP, FU>(fa, sm_f[warp][b], a.d, hashed, keepf)) {
+            ii = sm_i[warp][aa];
+            jj = sm_i[warp][b];
+            pass = replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj, ii < jj ? jj : ii);
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+        if (bal) {
+          unsigned long long b0 = 0;
+          if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)__popc(bal));
+          b0 = __shfl_sync(0xffffffffu, b0, 0) + __popc(bal & ((1u << lane) - 1u));
+          if (pass && b0 < (unsigned long long)a.cap)
+            a.cand[b0] = ((uint64_t)(ii < jj ? ii : jj) << 32) | (ii < jj ? jj : ii);
+        }
+      }
+      __syncwarp();
+    } else {
+      uint64_t J = (uint64_t)((sqrtf(8.0f * (float)local + 1.0f) - 1.0f) * 0.5f);
+      while (J * (J + 1) / 2 > local) --J;
+      while ((J + 1) * (J + 2) / 2 <= local) ++J;
+      const uint64_t I = local - J * (J + 1) / 2;
+      // the whole tile inside one run of equal full keys: every pair is
+      // equal on the first gap block, so none is reported under this K
+      if (subw) {
+        const uint32_t last = (uint32_t)min((uint64_t)len - 1, J * 32 + 31);
+        if (a.keys[st + (uint32_t)(I * 32)] == a.keys[st + last]) continue;
+      }
+      const uint32_t ra = (uint32_t)(I * 32 + lane);
+      const bool va = ra < len;
+      uint32_t fa[FP];
+      uint32_t ia = 0;
+#pragma unroll
+      for (int w = 0; w < FP; ++w) fa[w] = 0;
+      if (va) {
+        ia = a.vals[st + ra];
+        const uint2* src = reinterpret_cast<const uint2*>(pool + (size_t)ia * FP);
+#pragma unroll
+        for (int w = 0; w < FP; w += 2) {
+          const uint2 v = src[w / 2];
+          fa[w] = v.x;
+          fa[w + 1] = v.y;
+        }
+      }
+      const uint32_t cb = (uint32_t)(J * 32 + lane);
+      if (cb < len) {
+        const uint32_t idx = a.vals[st + cb];
+        sm_i[warp][lane] = idx;
+        const uint2* src = reinterpret_cast<const uint2*>(pool + (size_t)idx * FP);
+#pragma unroll
+        for (int w = 0; w < FP; w += 2) {
+          const uint2 v = src[w / 2];
+          sm_f[warp][lane][w] = v.x;
+          sm_f[warp][lane][w + 1] = v.y;
+        }
+      }
+      __syncwarp();
+      const uint32_t ncols = min(32u, len - (uint32_t)(J * 32));
+      // columns this lane may pair with: in range, and right of the
+      // diagonal on a diagonal tile
+      uint32_t valid = ncols == 32 ? 0xffffffffu : ((1u << ncols) - 1u);
+      if (I == J) valid &= (lane == 31) ? 0u : (0xffffffffu << (lane + 1));
+      if (!va) valid = 0;
+      uint32_t gpass = 0;
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c)
+        gpass |= (uint32_t)gaps_differ<FP, FU>(fa, sm_f[warp][c], gapf) << c;
+      gpass &= valid;
+      uint32_t passm = 0;
+      while (gpass) {
+        const int c = __ffs(gpass) - 1;
+        gpass &= gpass - 1;
+        if (fields_rest_ok<FP, FU>(fa, sm_f[warp][c], a.d, hashed, keepf)) {
           const uint32_t ib = sm_i[warp][c];
-          const uint32_t i0 = ia < ib ? ia : ib, j0 = ia < ib ? ib : ia;
-          if (pair_ok<W>(a, sm_gm[warp], ngap, keep, hashed, i0, j0, sa, sm_s[warp][c]))
+          if (replicates_ok_fields<FP>(a, fields, ia < ib ? ia : ib, ia < ib ? ib : ia))
             passm |= 1u << c;
         }
       }
@@ -388,15 +740,58 @@ check_kernel(CheckArgs a) {
       __syncwarp();
     }
   }
+  }
 }
 
 }  // namespace
 
+// Field layout of the strings: usable when every block fits 15 bits and the
+// blocks fit 8 words.  Returns the padded word count FP (even), or 0.
+int field_words(int ell, int k) {
+  if (k > kMaxFieldBlocks) return 0;
+  for (int b = 0; b < k; ++b) {
+    const int w = (int)((int64_t)(b + 1) * ell / k - (int64_t)b * ell / k);
+    if (w > 15) return 0;
+  }
+  const int F = (k + 1) / 2;
+  return (F + 1) & ~1;
+}
+
+int launch_fields(const uint64_t* strings, int64_t count, int ell, int k,
+                  uint32_t* fields, cudaStream_t s) {
+  const int FP = field_words(ell, k);
+  const int W = (ell + 63) / 64;
+  FieldLayout L;
+  L.k = k;
+  for (int b = 0; b < kMaxFieldBlocks; ++b) {
+    L.lo[b] = b < k ? (int)((int64_t)b * ell / k) : 0;
+    L.width[b] = b < k ? (int)((int64_t)(b + 1) * ell / k) - L.lo[b] : 0;
+  }
+  int64_t grid = (count + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (grid > cap) grid = cap;
+  kt_begin(KC_OTHER, s);
+#define MSM_FIELDS(WW, FF) \
+  if (W == WW && FP == FF) fields_kernel<WW, FF><<<(int)grid, 256, 0, s>>>(strings, count, L, fields)
+  MSM_FIELDS(1, 2); else MSM_FIELDS(1, 4); else MSM_FIELDS(1, 6); else MSM_FIELDS(1, 8);
+  else MSM_FIELDS(2, 2); else MSM_FIELDS(2, 4); else MSM_FIELDS(2, 6); else MSM_FIELDS(2, 8);
+  else MSM_FIELDS(3, 2); else MSM_FIELDS(3, 4); else MSM_FIELDS(3, 6); else MSM_FIELDS(3, 8);
+  else MSM_FIELDS(4, 2); else MSM_FIELDS(4, 4); else MSM_FIELDS(4, 6); else MSM_FIELDS(4, 8);
+  else {
+    kt_end(s);
+    return set_error("no field layout for ell=%d k=%d", ell, k), MSM_E_INVAL;
+  }
+#undef MSM_FIELDS
+  kt_end(s);
+  MSM_LAUNCH("fields_kernel");
+  return MSM_OK;
+}
+
 size_t pairs_scratch_bytes(int64_t items) {
   int64_t chunks = (items + kChunk - 1) / kChunk;
   int64_t maxg = items / 2 + 1;
-  return 4 * align256(4 * (size_t)chunks) + 2 * align256(4 * (size_t)maxg) +
-         2 * align256(8 * (size_t)maxg) + 512 +
+  return 4 * align256(4 * (size_t)chunks) + 3 * align256(4 * (size_t)maxg) +
+         2 * align256(8 * (size_t)maxg) + 768 +
          scan_scratch_bytes(maxg > chunks ? maxg : chunks) + 256;
 }
 
@@ -406,7 +801,7 @@ int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
   const int64_t chunks = (items + kChunk - 1) / kChunk;
   GroupWs g = carve(ws, items);
   kt_begin(KC_BOUNDS, s);
-  run_count_kernel<<<(unsigned)chunks, kThreads, 0, s>>>(b.keys, items, b.n,
+  run_count_kernel<<<(unsigned)chunks, kThreads, 0, s>>>(b.keys, items, b.n, b.masks,
                                                         g.cnt_start, g.cnt_end);
   kt_end(s);
   MSM_LAUNCH("run_count_kernel");
@@ -416,7 +811,7 @@ int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
   if (rc) return rc;
   kt_begin(KC_BOUNDS, s);
   run_write_kernel<<<(unsigned)chunks, kThreads, 0, s>>>(
-      b.keys, items, b.n, g.off_start, g.off_end, g.starts, g.ends, chunks,
+      b.keys, items, b.n, b.masks, g.off_start, g.off_end, g.starts, g.ends, chunks,
       g.cnt_start, g.ngroups);
   kt_end(s);
   MSM_LAUNCH("run_write_kernel");
@@ -426,8 +821,15 @@ int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
                                             checks_dev);
   kt_end(s);
   MSM_LAUNCH("run_work_kernel");
-  return exclusive_scan_u64_devlen(g.work, g.work_prefix, items / 2 + 1,
-                                   g.ngroups, g.scan_ws, g.total_work, s);
+  rc = exclusive_scan_u64_devlen(g.work, g.work_prefix, items / 2 + 1,
+                                 g.ngroups, g.scan_ws, g.total_work, s);
+  if (rc) return rc;
+  kt_begin(KC_BOUNDS, s);
+  chunk_index_kernel<<<grid, kThreads, 0, s>>>(g.work_prefix, g.ngroups, g.total_work,
+                                               (uint64_t)(items / 2 + 1), g.chunk_group);
+  kt_end(s);
+  MSM_LAUNCH("chunk_index_kernel");
+  return MSM_OK;
 }
 
 int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
@@ -435,6 +837,10 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   const int64_t items = b.n * b.S;
   GroupWs g = carve(ws, items);
   CheckArgs a{};
+  a.keys = b.keys;
+  a.chunk_group = g.chunk_group;
+  a.grab = g.grab;
+  a.chunk_cap = (uint64_t)(items / 2 + 1);
   a.vals = b.vals;
   a.starts = g.starts;
   a.ends = g.ends;
@@ -453,7 +859,24 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   a.cap = cap;
   a.count = count_dev;
   int grid = num_sms() * 6;
+  MSM_CUDA(cudaMemsetAsync(g.grab, 0, sizeof(unsigned), s));
   kt_begin(KC_CHECK, s);
+  if (b.fields) {
+    switch (b.FU) {  // words holding fields: ceil(k / 2)
+      case 1: check_fields_kernel<2, 1><<<grid, kThreads, 0, s>>>(a, b.fields); break;
+      case 2: check_fields_kernel<2, 2><<<grid, kThreads, 0, s>>>(a, b.fields); break;
+      case 3: check_fields_kernel<4, 3><<<grid, kThreads, 0, s>>>(a, b.fields); break;
+      case 4: check_fields_kernel<4, 4><<<grid, kThreads, 0, s>>>(a, b.fields); break;
+      case 5: check_fields_kernel<6, 5><<<grid, kThreads, 0, s>>>(a, b.fields); break;
+      case 6: check_fields_kernel<6, 6><<<grid, kThreads, 0, s>>>(a, b.fields); break;
+      case 7: check_fields_kernel<8, 7><<<grid, kThreads, 0, s>>>(a, b.fields); break;
+      case 8: check_fields_kernel<8, 8><<<grid, kThreads, 0, s>>>(a, b.fields); break;
+      default: kt_end(s); return set_error("bad field word count"), MSM_E_INVAL;
+    }
+    kt_end(s);
+    MSM_LAUNCH("check_fields_kernel");
+    return MSM_OK;
+  }
   switch (b.W) {
     case 1: check_kernel<1><<<grid, kThreads, 0, s>>>(a); break;
     case 2: check_kernel<2><<<grid, kThreads, 0, s>>>(a); break;

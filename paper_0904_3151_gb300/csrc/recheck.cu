@@ -58,42 +58,63 @@ __device__ double exact_distance(const void* X, int dtype, int64_t i,
   return sqrt(s);
 }
 
-// Decision from the float-path sum S'.  Returns the distance to report and
-// sets *decided_exact when the double-precision reference was needed.
+// Float-path decision from S' (relative error <= relS) and the float row
+// norms (each within u of the true norm).  Everything here is float: the
+// FP64 pipe of this GPU is narrow, and a per-pair double evaluation made the
+// recheck FP64-bound.  Error of the cosine value (S' - T') / (2 n_i n_j):
+//   S' contributes <= 2 relS (S - T) because T <= S/2 is required;
+//   T' = (n_i' - n_j')^2 is off by <= 4 u |n_i' - n_j'| (n_i + n_j)
+//        + 8 u^2 (n_i + n_j)^2 + 2 u T' (rounded norms, square);
+//   the subtraction, product and division add <= 5 u more.
+// The double-precision reference itself is within (dim + 8) 2^-51 of the
+// true value.  Returns false when the float path cannot settle the
+// comparison (too close to eps) or cannot guarantee 4e-6 relative accuracy
+// of the reported distance (need_accuracy); the caller then evaluates the
+// distance by its definition in double precision.
+__device__ __forceinline__ bool decide_fast(float S, float ni, float nj,
+                                            int metric, int dim, float eps,
+                                            float relS, bool need_accuracy,
+                                            float* delta_out, bool* keep) {
+  const float u = 0x1.0p-24f;
+  float delta, rel, abs_err;
+  if (metric == MSM_COSINE) {
+    const float dn = ni - nj;
+    const float T = dn * dn;
+    if (T > 0.5f * S) return false;
+    const float num = S - T;
+    if (!(num > 0.f)) return false;
+    const float sn = ni + nj;
+    const float errT = 4.f * u * fabsf(dn) * sn + 8.f * u * u * sn * sn + 2.f * u * T;
+    delta = num / (2.f * ni * nj);
+    rel = 2.5f * relS + 8.f * u + errT / num;
+    abs_err = (float)(dim + 8) * 0x1.0p-51f;
+  } else {
+    delta = sqrtf(S);
+    rel = 0.5f * relS + 2.f * u + (float)(dim + 4) * 0x1.0p-52f;
+    abs_err = 0.f;
+  }
+  if (need_accuracy && rel > 4e-6f) return false;
+  const float margin = rel * delta + abs_err + 1e-30f;
+  if (fabsf(delta - eps) <= margin) return false;
+  *delta_out = delta;
+  *keep = delta <= eps;
+  return true;
+}
+
+// Decision for one pair: float path, else the double-precision definition.
 __device__ __forceinline__ double decide(const void* X, int dtype, int64_t i,
                                          int64_t j, int dim, int metric,
-                                         double eps, float S, double ni,
-                                         double nj, double relS, bool* keep,
-                                         bool* exact) {
-  double Sd = (double)S;
-  double delta, margin;
-  bool fallback = false;
-  if (metric == MSM_COSINE) {
-    double dn = ni - nj;
-    double T = dn * dn;
-    if (T > 0.5 * Sd) {
-      fallback = true;
-      delta = 0.0;
-      margin = 0.0;
-    } else {
-      double den = 2.0 * ni * nj;
-      delta = (Sd - T) / den;
-      // relative error of S' doubled by the subtraction, the norms' double
-      // rounding through T, and the reference's own rounding (dim + 8) 2^-52
-      margin = 2.5 * relS * delta + 8.0 * (ni + nj) * sqrt(Sd) * 0x1.0p-52 / den +
-               (double)(dim + 8) * 0x1.0p-51;
-    }
-  } else {
-    delta = sqrt(Sd);
-    margin = (0.5 * relS + (double)(dim + 4) * 0x1.0p-52) * delta + 1e-300;
-  }
-  if (fallback || fabs(delta - eps) <= margin) {
-    delta = exact_distance(X, dtype, i, j, dim, metric);
-    *exact = true;
-  } else {
+                                         float eps, float S, float ni, float nj,
+                                         float relS, bool need_accuracy,
+                                         bool* keep, bool* exact) {
+  float d32;
+  if (decide_fast(S, ni, nj, metric, dim, eps, relS, need_accuracy, &d32, keep)) {
     *exact = false;
+    return (double)d32;
   }
-  *keep = delta <= eps;
+  const double delta = exact_distance(X, dtype, i, j, dim, metric);
+  *exact = true;
+  *keep = delta <= (double)eps;
   return delta;
 }
 
@@ -135,10 +156,10 @@ __device__ __forceinline__ float group_sq_dist(const void* X, int dtype,
 // 4 pairs per warp (8 lanes each), grid-stride over the candidates.
 __global__ void __launch_bounds__(kThreads)
 recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
-               double eps, const double* nrm64, const uint64_t* cand,
+               float eps, const float* nrm, const uint64_t* cand,
                const unsigned long long* m_dev, int64_t m_max,
                uint64_t* pairs_out, float* dist_out, unsigned long long* count,
-               unsigned long long* recompute, double relS) {
+               unsigned long long* recompute, float relS) {
   int64_t m = m_max;
   if (m_dev) m = min(m, (int64_t)*m_dev);
   const int lane = threadIdx.x & 31, sl = lane & 7, grp = lane >> 3;
@@ -146,26 +167,26 @@ recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nre = 0;
   for (int64_t base = warp * 4; base < m; base += nwarps * 4) {
-    int64_t t = base + grp;
-    bool valid = t < m;
-    uint64_t pr = valid ? cand[t] : 0;
-    int64_t i = (int64_t)(pr >> 32), j = (int64_t)(pr & 0xffffffffu);
-    float S = group_sq_dist(X, dtype, valid ? i : 0, valid ? j : 0, dim, sl);
+    const int64_t t = base + grp;
+    const bool valid = t < m;
+    const uint64_t pr = valid ? cand[t] : 0;
+    const int64_t i = (int64_t)(pr >> 32), j = (int64_t)(pr & 0xffffffffu);
+    const float S = group_sq_dist(X, dtype, valid ? i : 0, valid ? j : 0, dim, sl);
     bool keep = false, exact = false;
     double delta = 0.0;
     if (valid && sl == 0) {
-      double ni = metric == MSM_COSINE ? nrm64[i] : 0.0;
-      double nj = metric == MSM_COSINE ? nrm64[j] : 0.0;
-      delta = decide(X, dtype, i, j, dim, metric, eps, S, ni, nj, relS, &keep, &exact);
+      const float ni = metric == MSM_COSINE ? nrm[i] : 0.f;
+      const float nj = metric == MSM_COSINE ? nrm[j] : 0.f;
+      delta = decide(X, dtype, i, j, dim, metric, eps, S, ni, nj, relS, true, &keep, &exact);
       nre += exact;
     }
-    unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (bal) {
       unsigned long long b0 = 0;
       if (lane == 0) b0 = atomicAdd(count, (unsigned long long)__popc(bal));
       b0 = __shfl_sync(0xffffffffu, b0, 0);
       if (keep) {
-        unsigned long long slot = b0 + __popc(bal & ((1u << lane) - 1u));
+        const unsigned long long slot = b0 + __popc(bal & ((1u << lane) - 1u));
         if (pairs_out) pairs_out[slot] = pr;
         if (dist_out) dist_out[slot] = (float)delta;
       }
@@ -180,8 +201,8 @@ recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
 constexpr int TB = 64, TK = 32;
 __global__ void __launch_bounds__(256)
 eps_count_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
-                 double eps, const double* nrm64, unsigned long long* count,
-                 double relS) {
+                 float eps, const float* nrm, unsigned long long* count,
+                 float relS) {
   __shared__ float Xi[TB][TK + 1];
   __shared__ float Xj[TB][TK + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -192,7 +213,7 @@ eps_count_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
     int64_t J = (int64_t)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
     while (J * (J + 1) / 2 > tile) --J;
     while ((J + 1) * (J + 2) / 2 <= tile) ++J;
-    int64_t I = tile - J * (J + 1) / 2;
+    const int64_t I = tile - J * (J + 1) / 2;
     float acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -200,9 +221,9 @@ eps_count_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
       for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
     for (int k0 = 0; k0 < dim; k0 += TK) {
       for (int e = tid; e < TB * TK; e += 256) {
-        int r = e / TK, cc = e % TK;
-        int64_t ri = I * TB + r, rj = J * TB + r;
-        int kk = k0 + cc;
+        const int r = e / TK, cc = e % TK;
+        const int64_t ri = I * TB + r, rj = J * TB + r;
+        const int kk = k0 + cc;
         Xi[r][cc] = (ri < n && kk < dim) ? ldx(X, dtype, ri * dim + kk) : 0.f;
         Xj[r][cc] = (rj < n && kk < dim) ? ldx(X, dtype, rj * dim + kk) : 0.f;
       }
@@ -218,7 +239,7 @@ eps_count_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
-            float t = av[a] - bv[b];
+            const float t = av[a] - bv[b];
             acc[a][b] = fmaf(t, t, acc[a][b]);
           }
       }
@@ -228,12 +249,12 @@ eps_count_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        int64_t i = I * TB + ty * 4 + a, j = J * TB + tx * 4 + b;
+        const int64_t i = I * TB + ty * 4 + a, j = J * TB + tx * 4 + b;
         if (i < n && j < n && i < j) {
-          double ni = metric == MSM_COSINE ? nrm64[i] : 0.0;
-          double nj = metric == MSM_COSINE ? nrm64[j] : 0.0;
+          const float ni = metric == MSM_COSINE ? nrm[i] : 0.f;
+          const float nj = metric == MSM_COSINE ? nrm[j] : 0.f;
           bool keep, exact;
-          decide(X, dtype, i, j, dim, metric, eps, acc[a][b], ni, nj, relS, &keep, &exact);
+          decide(X, dtype, i, j, dim, metric, eps, acc[a][b], ni, nj, relS, false, &keep, &exact);
           c += keep;
         }
       }
@@ -246,21 +267,20 @@ eps_count_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
 }  // namespace
 
 int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
-                   float eps, const double* nrm64, const uint64_t* cand,
+                   float eps, const float* nrm, const uint64_t* cand,
                    const unsigned long long* m_dev, int64_t m_max,
                    uint64_t* pairs_out, float* dist_out,
                    unsigned long long* count_dev,
                    unsigned long long* recompute_dev, cudaStream_t s) {
   if (m_max <= 0) return MSM_OK;
-  int64_t warps = (m_max + 3) / 4;
+  const int64_t warps = (m_max + 3) / 4;
   int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
-  int64_t cap = (int64_t)num_sms() * 8;
+  const int64_t cap = (int64_t)num_sms() * 8;
   if (grid > cap) grid = cap;
-  double relS = 10.0 * kU;
+  const float relS = 10.f * (float)kU;
   kt_begin(KC_RECHECK, s);
-  recheck_kernel<<<(int)grid, kThreads, 0, s>>>(X, dtype, n, dim, metric,
-                                                (double)eps, nrm64, cand, m_dev,
-                                                m_max, pairs_out, dist_out,
+  recheck_kernel<<<(int)grid, kThreads, 0, s>>>(X, dtype, n, dim, metric, eps, nrm, cand,
+                                                m_dev, m_max, pairs_out, dist_out,
                                                 count_dev, recompute_dev, relS);
   kt_end(s);
   MSM_LAUNCH("recheck_kernel");
@@ -268,16 +288,16 @@ int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
 }
 
 int launch_eps_count(const void* X, int dtype, int64_t n, int dim, int metric,
-                     float eps, const double* nrm64,
+                     float eps, const float* nrm,
                      unsigned long long* count_dev, cudaStream_t s) {
-  int64_t nb = (n + TB - 1) / TB;
-  int64_t ntiles = nb * (nb + 1) / 2;
+  const int64_t nb = (n + TB - 1) / TB;
+  const int64_t ntiles = nb * (nb + 1) / 2;
   int64_t grid = (int64_t)num_sms() * 8;
   if (grid > ntiles) grid = ntiles;
-  double relS = (double)(dim + 6) * kU;
+  const float relS = (float)(dim + 6) * (float)kU;
   kt_begin(KC_OTHER, s);
-  eps_count_kernel<<<(int)grid, 256, 0, s>>>(X, dtype, n, dim, metric,
-                                             (double)eps, nrm64, count_dev, relS);
+  eps_count_kernel<<<(int)grid, 256, 0, s>>>(X, dtype, n, dim, metric, eps, nrm, count_dev,
+                                             relS);
   kt_end(s);
   MSM_LAUNCH("eps_count_kernel");
   return MSM_OK;

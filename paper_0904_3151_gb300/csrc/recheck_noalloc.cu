@@ -82,7 +82,7 @@ extern "C" int msm_recheck_noalloc(const void* X, int64_t n, int dim, int dtype,
   if (f & 2u) return set_error("input contains NaN or Inf"), MSM_E_NONFINITE;
   if ((f & 1u) && metric == MSM_COSINE)
     return set_error("cosine distance is undefined for an all-zero row"), MSM_E_ZERO_NORM;
-  rc = launch_recheck(X, dtype, n, dim, metric, eps, n64, cand, nullptr, m,
+  rc = launch_recheck(X, dtype, n, dim, metric, eps, n32, cand, nullptr, m,
                       pairs_out, dist_out, ctr, ctr + 1, s);
   if (rc) return rc;
   unsigned long long h[2] = {0, 0};

@@ -4,6 +4,7 @@ Integer and index results (strings, pair lists, counts) must match bit for
 bit; distances within 1e-5 relative of the oracle's double-precision value
 (plus that value's own cancellation error, (dim + 8) 2^-51 for Eq. 2).
 """
+import itertools
 import math
 
 import numpy as np
@@ -133,11 +134,25 @@ def test_enumerate_bit_exact(msm, n, ell, k, d, Q, nc, flip):
     assert np.array_equal(got, want)          # canonical order: identical arrays
     assert st["cand"] == len(want)
     assert st["masks"] == ost["masks"]
-    widths = [(b + 1) * ell // k - b * ell // k for b in range(k)]
-    if sum(sorted(widths)[-(k - d):]) <= 32:  # exact grouping keys
+    if _keys_exact(ell, k, d):
         assert st["checks"] == ost["checks"]
     else:
         assert st["checks"] >= ost["checks"]
+
+
+def _keys_exact(ell, k, d):
+    """Whether the library's automatic grouping key holds every kept block
+    set exactly (then the in-group pair count equals the oracle's): with a
+    first-gap sub-key (some grouping has gap blocks, blocks <= 16 bits) the
+    key is 32 bits and the kept bits plus the first gap block must fit;
+    otherwise the kept bits must fit 24."""
+    widths = [(b + 1) * ell // k - b * ell // k for b in range(k)]
+    masks = list(itertools.combinations(range(k), k - d))
+    gaps = [[b for b in range(max(K)) if b not in K] for K in masks]
+    if any(gaps) and max(widths) <= 16:
+        return all(sum(widths[b] for b in K) + (widths[g[0]] if g else 0) <= 32
+                   for K, g in zip(masks, gaps))
+    return max(sum(widths[b] for b in K) for K in masks) <= 24
 
 
 def test_enumerate_one_large_group(msm):
@@ -228,7 +243,8 @@ def _eps_graph_case(msm, wl, Q, n=None, dtype="f32", **kw):
 def test_eps_graph_small_workload(msm):
     """The 20,000 x 64 workload (l=64, k=8, d=4, cosine eps=0.15)."""
     wl = W.WORKLOADS["small"]
-    X, pairs, dist, st, want, wd, info = _eps_graph_case(msm, wl, Q=7)
+    # 32-bit exact grouping keys, so the inspected-pair count is the oracle's
+    X, pairs, dist, st, want, wd, info = _eps_graph_case(msm, wl, Q=7, group_bits=32)
     assert np.array_equal(_u64(pairs), want)
     assert np.allclose(dist.cpu().numpy().astype(np.float64), wd, **_dist_tol(wl.dim))
     assert st["cand"] == info["cand"]
