@@ -159,9 +159,11 @@ def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
               Q: int = 0, miss_ratio: float = 1e-6, R: torch.Tensor | None = None,
               seed: int = 0, out_mode: int = OUT_PAIRS_DIST, canonical: bool = False,
               group_bits: int = 0, cand_capacity: int = 0, simt_projection: bool = False,
-              device=None):
+              Y: torch.Tensor | None = None, device=None):
     """The whole method.  X may be a CUDA tensor or a (pinned) CPU tensor,
-    which the library copies in.  Returns (pairs, dist, stats)."""
+    which the library copies in.  With Y (CUDA [n][dim_y], e.g. learned
+    features) the strings come from Y while the recheck uses X.
+    Returns (pairs, dist, stats)."""
     assert X.is_contiguous() and X.dim() == 2
     n, dim = X.shape
     dev = X.device if X.is_cuda else torch.device(device or "cuda")
@@ -169,6 +171,9 @@ def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
     p.ell, p.k, p.d, p.Q = ell, k, d, Q
     p.seed = seed
     p.R = R.data_ptr() if R is not None else None
+    if Y is not None:
+        assert Y.is_cuda and Y.is_contiguous() and Y.shape[0] == n
+        p.Y, p.dim_y, p.dtype_y = Y.data_ptr(), Y.shape[1], _dtype(Y)
     p.out_mode = out_mode
     p.flags = (FLAG_CANONICAL if canonical else 0) | (FLAG_SIMT_PROJECTION if simt_projection else 0)
     p.group_bits = group_bits
@@ -186,6 +191,84 @@ def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
     s = st.as_dict()
     s["count"] = int(out.count)
     return pairs, dist, s
+
+
+class MLPProjection:
+    """Learned feature map y = W2 gelu(W1 x + b1) + b2 (bf16 weights, float
+    master copy and Adam moments), trained with the library's kernels on
+    pairs labelled neighbour / non-neighbour."""
+
+    def __init__(self, dim: int, hidden: int = 512, dim_out: int = 128, seed: int = 0,
+                 device="cuda"):
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        W1 = torch.randn(hidden, dim, generator=g) / dim ** 0.5
+        W2 = torch.randn(dim_out, hidden, generator=g) / hidden ** 0.5
+        self.dim, self.hidden, self.dim_out = dim, hidden, dim_out
+        self.params = torch.cat([W1.reshape(-1), torch.zeros(hidden), W2.reshape(-1),
+                                 torch.zeros(dim_out)]).to(device)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.W1h = W1.to(device, torch.bfloat16).contiguous()
+        self.W2h = W2.to(device, torch.bfloat16).contiguous()
+        self.step = 0
+
+    def _views(self):
+        h, d, o = self.hidden, self.dim, self.dim_out
+        b1 = self.params[h * d: h * d + h]
+        b2 = self.params[h * d + h + o * h:]
+        return b1, b2
+
+    def features(self, X: torch.Tensor) -> torch.Tensor:
+        assert X.is_cuda and X.is_contiguous() and X.shape[1] == self.dim
+        b1, b2 = self._views()
+        Y = torch.empty((X.shape[0], self.dim_out), dtype=torch.float32, device=X.device)
+        _check(lib().msm_mlp_forward(ctypes.c_void_p(X.data_ptr()), X.shape[0], self.dim, _dtype(X),
+                                     ctypes.c_void_p(self.W1h.data_ptr()),
+                                     ctypes.c_void_p(b1.data_ptr()),
+                                     ctypes.c_void_p(self.W2h.data_ptr()),
+                                     ctypes.c_void_p(b2.data_ptr()), self.hidden, self.dim_out,
+                                     ctypes.c_void_p(Y.data_ptr()), _stream()), "msm_mlp_forward")
+        return Y
+
+    def grad(self, X, pi, pj, label, m_pos=0.98, m_neg=0.5):
+        """(loss, grads) of one batch; pi, pj int32 CUDA, label uint8 CUDA."""
+        b1, b2 = self._views()
+        grads = torch.empty_like(self.params)
+        loss = ctypes.c_float(0.0)
+        _check(lib().msm_mlp_grad(ctypes.c_void_p(X.data_ptr()), X.shape[0], self.dim, _dtype(X),
+                                  ctypes.c_void_p(self.W1h.data_ptr()), ctypes.c_void_p(b1.data_ptr()),
+                                  ctypes.c_void_p(self.W2h.data_ptr()), ctypes.c_void_p(b2.data_ptr()),
+                                  self.hidden, self.dim_out, ctypes.c_void_p(pi.data_ptr()),
+                                  ctypes.c_void_p(pj.data_ptr()), ctypes.c_void_p(label.data_ptr()),
+                                  pi.numel(), ctypes.c_float(m_pos), ctypes.c_float(m_neg),
+                                  ctypes.c_void_p(grads.data_ptr()), ctypes.byref(loss), _stream()),
+               "msm_mlp_grad")
+        return loss.value, grads
+
+    def adam(self, grads, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step += 1
+        _check(lib().msm_mlp_adam(ctypes.c_void_p(self.params.data_ptr()),
+                                  ctypes.c_void_p(grads.data_ptr()), ctypes.c_void_p(self.m.data_ptr()),
+                                  ctypes.c_void_p(self.v.data_ptr()), self.params.numel(), self.step,
+                                  ctypes.c_float(lr), ctypes.c_float(beta1), ctypes.c_float(beta2),
+                                  ctypes.c_float(eps), ctypes.c_void_p(self.W1h.data_ptr()),
+                                  ctypes.c_void_p(self.W2h.data_ptr()), self.hidden, self.dim,
+                                  self.dim_out, _stream()), "msm_mlp_adam")
+
+    def train(self, X, pi, pj, label, steps=200, batch=4096, lr=1e-3, m_pos=0.98,
+              m_neg=0.5, seed=0):
+        """Minibatch Adam over the labelled pairs (CUDA int32 pi, pj, uint8
+        label); returns the loss history."""
+        g = torch.Generator(device=X.device).manual_seed(seed)
+        hist = []
+        for _ in range(steps):
+            sel = torch.randint(0, pi.numel(), (min(batch, pi.numel()),), device=X.device,
+                                generator=g)
+            loss, grads = self.grad(X, pi[sel].contiguous(), pj[sel].contiguous(),
+                                    label[sel].contiguous(), m_pos, m_neg)
+            self.adam(grads, lr)
+            hist.append(loss)
+        return hist
 
 
 def eps_count_exhaustive(X: torch.Tensor, metric, eps: float) -> int:

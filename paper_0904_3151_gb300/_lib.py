@@ -52,7 +52,8 @@ class Params(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_int), ("k", ctypes.c_int), ("d", ctypes.c_int), ("Q", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("R", ctypes.c_void_p), ("out_mode", ctypes.c_int),
                 ("flags", ctypes.c_int), ("group_bits", ctypes.c_int), ("reserved", ctypes.c_int),
-                ("cand_capacity", ctypes.c_int64)]
+                ("cand_capacity", ctypes.c_int64), ("Y", ctypes.c_void_p), ("dim_y", ctypes.c_int),
+                ("dtype_y", ctypes.c_int)]
 
 
 # Every symbol include/msm.h declares, with its ctypes signature.
@@ -81,6 +82,15 @@ SIGNATURES = {
                                      ctypes.POINTER(Allocator), ctypes.POINTER(Pairs),
                                      ctypes.POINTER(Stats), vp]),
     "msm_free_pairs": (None, [ctypes.POINTER(Pairs), ctypes.POINTER(Allocator), vp]),
+    "msm_mlp_forward": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, vp, vp,
+                                       vp, ctypes.c_int, ctypes.c_int, vp, vp]),
+    "msm_mlp_grad": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
+                                    ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_int64,
+                                    ctypes.c_float, ctypes.c_float, vp,
+                                    ctypes.POINTER(ctypes.c_float), vp]),
+    "msm_mlp_adam": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, vp,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]),
     "msm_eps_count_exhaustive": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_float, i64p, vp]),
 }

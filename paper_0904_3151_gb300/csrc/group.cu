@@ -203,19 +203,26 @@ scatter_kernel(SortArgs a) {
 
   KeyT key[IPT];
   uint32_t val[IPT], rank[IPT];
+  // all loads first (independent, so they are in flight together), then
+  // the ranking, whose warp-synchronous steps would serialise them
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const int e = warp * PER_WARP + r * 32 + lane;
+    key[r] = 0;
+    val[r] = 0;
+    if (e < cnt) {
+      key[r] = load_key<KeyT, FROM_STR>(a, kl, seg, base + e);
+      if constexpr (FROM_STR) val[r] = (uint32_t)(base + e);
+      else val[r] = a.vals_in ? a.vals_in[(int64_t)seg * a.n + base + e] : 0u;
+    }
+  }
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
     int e = warp * PER_WARP + r * 32 + lane;
     bool valid = e < cnt;
-    KeyT k = 0;
-    uint32_t v = 0;
-    uint32_t digit = 0xFFFFFFFFu;
-    if (valid) {
-      k = load_key<KeyT, FROM_STR>(a, kl, seg, base + e);
-      if constexpr (FROM_STR) v = (uint32_t)(base + e);
-      else v = a.vals_in ? a.vals_in[(int64_t)seg * a.n + base + e] : 0u;
-      digit = (uint32_t)(k >> a.shift) & 0xFFu;
-    }
+    const KeyT k = key[r];
+    const uint32_t v = val[r];
+    uint32_t digit = valid ? ((uint32_t)(k >> a.shift) & 0xFFu) : 0xFFFFFFFFu;
     unsigned peers = __match_any_sync(0xffffffffu, digit);
     int leader = __ffs(peers) - 1;
     uint32_t old = 0;
@@ -223,8 +230,6 @@ scatter_kernel(SortArgs a) {
     old = __shfl_sync(0xffffffffu, old, leader);
     if (valid && lane == leader) wh[warp][digit] = old + __popc(peers);
     __syncwarp();
-    key[r] = k;
-    val[r] = v;
     rank[r] = old + __popc(peers & lt_mask);
   }
   __syncthreads();

@@ -1,11 +1,11 @@
 // Step A8 (Sec. 4.1, last step): exact distance test of each candidate pair
 // in E, keeping Delta(x_i, x_j) <= eps (Def. 1.1, inclusive).
 //
-// Fast path (float): S = sum_c (x_ic - x_jc)^2, each lane of an 8-lane group
+// Fast path (float): S = sum_c (x_ic - x_jc)^2, each lane of a 4-lane group
 // summing its share of coordinates with compensated (Kahan) summation, then
-// a 3-level shuffle tree.  Every term carries at most 3 roundings
-// (difference, square, and the compensated sum's 2u) and the tree adds 3,
-// so |S' - S| <= 8u S + O(u^2) with u = 2^-24.
+// a 2-level shuffle tree.  Every term carries at most 3 roundings
+// (difference, square, and the compensated sum's 2u) and the tree adds at
+// most 3, so |S' - S| <= 8u S + O(u^2) with u = 2^-24.
 //   Euclidean: Delta = sqrt(S).
 //   Cosine (Eq. 2): from |x_i - x_j|^2 = |x_i|^2 + |x_j|^2 - 2 x_i.x_j,
 //     Delta = (S - (|x_i| - |x_j|)^2) / (2 |x_i| |x_j|), norms in double;
@@ -119,6 +119,18 @@ __device__ __forceinline__ double decide(const void* X, int dtype, int64_t i,
 }
 
 // Sum of squared differences of rows i and j by the 8 lanes of a group.
+__device__ __forceinline__ void kahan_add(float v, float& acc, float& comp) {
+  const float y = v - comp;
+  const float s = acc + y;
+  comp = (s - acc) - y;
+  acc = s;
+}
+
+// Sum of squared differences of rows i and j by the G lanes of a group.
+// Float rows: each lane first issues 4 float4 loads per row, then adds, so
+// 8 independent 16-byte loads per lane are in flight (the kernel is bound
+// by gather latency).
+template <int G>
 __device__ __forceinline__ float group_sq_dist(const void* X, int dtype,
                                                int64_t i, int64_t j, int dim,
                                                int sl) {
@@ -127,51 +139,56 @@ __device__ __forceinline__ float group_sq_dist(const void* X, int dtype,
   if (dtype == MSM_DT_F32 && (dim & 3) == 0) {
     const float4* xi = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + bi);
     const float4* xj = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + bj);
-    for (int c4 = sl; c4 < dim / 4; c4 += 8) {
-      float4 a = __ldg(xi + c4), b = __ldg(xj + c4);
-      float t[4] = {a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w};
+    const int n4 = dim / 4;
+    for (int c0 = sl; c0 < n4; c0 += 4 * G) {
+      float4 a[4], b[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        float y = __fmul_rn(t[u], t[u]) - comp;
-        float s = acc + y;
-        comp = (s - acc) - y;
-        acc = s;
+        const int c4 = c0 + u * G;
+        a[u] = c4 < n4 ? __ldg(xi + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        b[u] = c4 < n4 ? __ldg(xj + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float t0 = a[u].x - b[u].x, t1 = a[u].y - b[u].y;
+        const float t2 = a[u].z - b[u].z, t3 = a[u].w - b[u].w;
+        kahan_add(__fmul_rn(t0, t0), acc, comp);
+        kahan_add(__fmul_rn(t1, t1), acc, comp);
+        kahan_add(__fmul_rn(t2, t2), acc, comp);
+        kahan_add(__fmul_rn(t3, t3), acc, comp);
       }
     }
   } else {
-    for (int c = sl; c < dim; c += 8) {
-      float t = ldx(X, dtype, bi + c) - ldx(X, dtype, bj + c);
-      float y = __fmul_rn(t, t) - comp;
-      float s = acc + y;
-      comp = (s - acc) - y;
-      acc = s;
+    for (int c = sl; c < dim; c += G) {
+      const float t = ldx(X, dtype, bi + c) - ldx(X, dtype, bj + c);
+      kahan_add(__fmul_rn(t, t), acc, comp);
     }
   }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc;
 }
 
-// 4 pairs per warp (8 lanes each), grid-stride over the candidates.
+// 8 pairs per warp (4 lanes each), grid-stride over the candidates.
 __global__ void __launch_bounds__(kThreads)
 recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
                float eps, const float* nrm, const uint64_t* cand,
                const unsigned long long* m_dev, int64_t m_max,
                uint64_t* pairs_out, float* dist_out, unsigned long long* count,
                unsigned long long* recompute, float relS) {
+  constexpr int G = 4;  // lanes per pair: 8 pairs per warp in flight
   int64_t m = m_max;
   if (m_dev) m = min(m, (int64_t)*m_dev);
-  const int lane = threadIdx.x & 31, sl = lane & 7, grp = lane >> 3;
+  const int lane = threadIdx.x & 31, sl = lane & (G - 1), grp = lane / G;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nre = 0;
-  for (int64_t base = warp * 4; base < m; base += nwarps * 4) {
+  for (int64_t base = warp * (32 / G); base < m; base += nwarps * (32 / G)) {
     const int64_t t = base + grp;
     const bool valid = t < m;
     const uint64_t pr = valid ? cand[t] : 0;
     const int64_t i = (int64_t)(pr >> 32), j = (int64_t)(pr & 0xffffffffu);
-    const float S = group_sq_dist(X, dtype, valid ? i : 0, valid ? j : 0, dim, sl);
+    const float S = group_sq_dist<G>(X, dtype, valid ? i : 0, valid ? j : 0, dim, sl);
     bool keep = false, exact = false;
     double delta = 0.0;
     if (valid && sl == 0) {
@@ -273,7 +290,7 @@ int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
                    unsigned long long* count_dev,
                    unsigned long long* recompute_dev, cudaStream_t s) {
   if (m_max <= 0) return MSM_OK;
-  const int64_t warps = (m_max + 3) / 4;
+  const int64_t warps = (m_max + 7) / 8;
   int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (grid > cap) grid = cap;

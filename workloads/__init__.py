@@ -80,6 +80,14 @@ def clustered(n: int, dim: int, n_clusters: int, sigma: float, seed: int,
     return out
 
 
+def clustered_split(n_first: int, n_second: int, dim: int, n_clusters: int,
+                    sigma: float, seed: int, normalise: bool = True):
+    """Two disjoint samples of the same mixture (same centres): the first
+    n_first and the next n_second points of one draw."""
+    X = clustered(n_first + n_second, dim, n_clusters, sigma, seed, normalise)
+    return X[:n_first], X[n_first:]
+
+
 def cluster_labels(n: int, n_clusters: int, seed: int, dim: int,
                    chunk: int = 1 << 18) -> np.ndarray:
     """The mixture component of every point drawn by ``clustered`` (same seed)."""
