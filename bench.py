@@ -43,7 +43,101 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-missing", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the bf16 and learned-projection forms")
     return ap.parse_args()
+
+
+def time_steps(fn, steps, stream):
+    """Device time per call of fn over `steps` calls (CUDA events)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = None
+    for _ in range(steps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, out
+
+
+def run_forms(msm, wl, X, Xh, n, Q, seed, truth, ratio_plain, ms_plain, steps, stream):
+    """The bf16-storage form and the learned-projection form on the same
+    workload, each at a measured missing-edge ratio no worse than the plain
+    form's."""
+    import torch
+    forms = {}
+    # bf16 storage: X rounded to bf16 (its own exhaustive truth)
+    Xb = X.to(torch.bfloat16)
+    tb = msm.eps_count_exhaustive(Xb, msm.COSINE, wl.eps)
+
+    def step_b():
+        return msm.eps_graph(Xb, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=Q, seed=seed,
+                             cand_capacity=600 * n)
+    step_b()
+    ms_b, (p, dv, st) = time_steps(step_b, steps, stream)
+    forms["bf16_storage"] = {
+        "value": n / (ms_b / 1000.0), "unit": UNIT, "ms_per_step": ms_b, "Q": Q,
+        "missing_ratio": (tb - st["count"]) / max(1, tb), "pairs": st["count"],
+        "speedup_vs_plain": ms_plain / ms_b,
+        "note": "X stored bf16: tcgen05 kind::f16 projection (R split hi+lo), recheck on bf16 rows"}
+    del p, dv, Xb
+    # learned projection, trained on a disjoint sample of the same mixture
+    t0 = time.perf_counter()
+    Xt = torch.from_numpy(W.clustered(n, wl.dim, wl.n_clusters, wl.sigma, wl.data_seed + 500,
+                                      centres_seed=wl.data_seed)).cuda()
+    pos, _, _ = msm.eps_graph(Xt, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=4, seed=seed + 1,
+                              out_mode=1, cand_capacity=600 * n)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    npos = min(pos.numel(), 1 << 21)
+    sel = torch.randint(0, pos.numel(), (npos,), device="cuda", generator=g)
+    P = pos[sel]
+    del pos
+    ri = torch.randint(0, n, (3 * npos,), device="cuda", generator=g)
+    rj = torch.randint(0, n, (3 * npos,), device="cuda", generator=g)
+    Xn = torch.nn.functional.normalize(Xt, dim=1)
+    far = (ri != rj) & (1.0 - (Xn[ri] * Xn[rj]).sum(1) > wl.eps)
+    ri, rj = ri[far][:npos], rj[far][:npos]
+    pi = torch.cat([P >> 32, ri]).to(torch.int32).contiguous()
+    pj = torch.cat([P & 0xFFFFFFFF, rj]).to(torch.int32).contiguous()
+    lab = torch.cat([torch.ones(npos, dtype=torch.uint8, device="cuda"),
+                     torch.zeros(ri.numel(), dtype=torch.uint8, device="cuda")])
+    net = msm.MLPProjection(wl.dim, 512, 128, seed=0)
+    hist = net.train(Xt, pi, pj, lab, steps=1000, batch=8192, lr=1e-2, m_pos=0.999, m_neg=0.2)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del Xt, Xn, pi, pj, lab, P
+    chosen = None
+    ladder = []
+    for Ql in range(1, Q + 1):
+        Y = net.features(X)
+        _, _, st = msm.eps_graph(X, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=Ql, seed=seed,
+                                 out_mode=2, Y=Y, cand_capacity=600 * n)
+        r = (truth - st["count"]) / max(1, truth)
+        ladder.append({"Q": Ql, "missing_ratio": r})
+        if r <= ratio_plain:
+            chosen = Ql
+            break
+    if chosen is not None:
+        def step_l():
+            Y = net.features(X)
+            return msm.eps_graph(X, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=chosen, seed=seed,
+                                 Y=Y, cand_capacity=600 * n)
+        step_l()
+        ms_l, (p, dv, st) = time_steps(step_l, steps, stream)
+        forms["learned"] = {
+            "value": n / (ms_l / 1000.0), "unit": UNIT, "ms_per_step": ms_l, "Q": chosen,
+            "missing_ratio": (truth - st["count"]) / max(1, truth), "pairs": st["count"],
+            "speedup_vs_plain": ms_plain / ms_l, "train_seconds": train_s,
+            "train_loss": [float(hist[0]), float(hist[-1])], "Q_ladder": ladder,
+            "note": "MLP 128-512-128 (gelu, bf16 weights) trained by the library's kernels on "
+                    "pairs the plain method finds on a disjoint 1M sample; step = features + "
+                    "eps-graph on the features' strings, recheck on x"}
+        del p, dv
+    else:
+        forms["learned"] = {"Q_ladder": ladder, "note": "no Q <= plain Q reached the plain ratio"}
+    return forms
 
 
 def workload_desc(wl, n, Q):
@@ -354,6 +448,12 @@ def main():
         missing = {"truth_pairs": truth, "found_pairs": counts[-1],
                    "ratio": (truth - counts[-1]) / max(1, truth)}
 
+    # ---- other forms of the method on the same workload (rank 0, N=1)
+    forms = None
+    if rank == 0 and world == 1 and not a.no_forms and missing is not None:
+        forms = run_forms(msm, wl, X, Xh, n, Q, seed, missing["truth_pairs"], missing["ratio"],
+                          ms, max(2, min(3, a.steps)), stream)
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -381,7 +481,7 @@ def main():
             "kernel_ms_per_step": {k: v / a.steps for k, v in kms.items()},
             "stats": {k: st[k] for k in ("Q", "masks", "checks", "cand", "type1",
                                          "proj_recompute", "dist_recompute", "overflow_retries")},
-            "missing_edges": missing, "cpu_baseline": cpu,
+            "missing_edges": missing, "forms": forms, "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)
     if dist:

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "msm_internal.cuh"
@@ -257,11 +258,17 @@ static int read_back(T* host, const T* dev, cudaStream_t s) {
 
 // A3-A7 over all replicates.  On success *cand (allocated from sc, owned by
 // sc) holds *count candidate pairs.
+// With a sink, every mask batch's candidates are handed to it (device
+// pointer, count) and the buffer restarts empty, so memory is bounded by one
+// batch; *count_out is then 0 and stats->cand the total handed over.
+using CandSink = std::function<int(const uint64_t*, int64_t)>;
+
 static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
                    int k, int d, int Q, int group_bits_req, int64_t cap0,
                    uint64_t** cand_out, int64_t* count_out, msm_stats* st,
-                   PhaseTimer& tm) {
+                   PhaseTimer& tm, const CandSink& sink = CandSink()) {
   cudaStream_t s = sc.stream();
+  int64_t total_cand = 0;
   const BlockLayout L = make_layout(ell, k);
   std::vector<MaskDesc> masks = make_masks(L, d);
   const int M = (int)masks.size();
@@ -388,8 +395,17 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
         MSM_CUDA(cudaStreamSynchronize(s));
         ++retries;
       }
+      if (sink) {
+        // hand this batch's candidates over and start the next batch empty
+        int rc = sink(cand, count);
+        if (rc) return rc;
+        total_cand += count;
+        count = 0;
+        MSM_CUDA(cudaMemsetAsync(count_dev, 0, sizeof(unsigned long long), s));
+      }
     }
   }
+  if (!sink) total_cand = count;
   if (st) {
     unsigned long long ch = 0;
     int rc = read_back(&ch, checks_dev, s);
@@ -397,7 +413,7 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
     st->Q = Q;
     st->masks = (int64_t)Q * M;
     st->checks = (int64_t)ch;
-    st->cand = count;
+    st->cand = total_cand;
     st->overflow_retries = retries;
   }
   *cand_out = cand;
@@ -723,13 +739,22 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
 
   uint64_t* cand = nullptr;
   int64_t m = 0;
+  const int mode = params->out_mode;
+  // Count only: each mask batch's candidates are rechecked as they come and
+  // dropped, so the candidate list never exceeds one batch.
+  CandSink sink;
+  if (mode == MSM_OUT_COUNT)
+    sink = [&](const uint64_t* c, int64_t cnt) -> int {
+      tm.mark(5);
+      return launch_recheck(Xd, dtype, n, dim, metric, eps, n32, c, nullptr, cnt, nullptr,
+                            nullptr, ctr, ctr + 1, s);
+    };
   rc = run_msm(sc, strings, n, ell, k, d, Q, params->group_bits,
-               params->cand_capacity, &cand, &m, stats, tm);
+               params->cand_capacity, &cand, &m, stats, tm, sink);
   if (rc) return rc;
   sc.put(strings);
 
   // A8: recheck into the output buffers.
-  const int mode = params->out_mode;
   uint64_t* pairs = nullptr;
   float* dist = nullptr;
   if (mode != MSM_OUT_COUNT && m > 0) {
@@ -761,7 +786,7 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
   if (stats) {
     tm.collect(stats->ms);
     kts.collect(stats->kernel_ms, stats->kernel_launches);
-    stats->type1 = m - kept;
+    stats->type1 = stats->cand - kept;
     stats->dist_recompute = (int64_t)h[1];
     stats->proj_recompute = (int64_t)h[2];
   }

@@ -133,16 +133,20 @@ def test_learned_projection_lowers_missing_ratio(msm):
     rng = np.random.default_rng(3)
     P = pos.cpu().numpy().view(np.uint64)
     P = P[rng.choice(len(P), min(len(P), 200000), replace=False)]
-    ri = rng.integers(0, n, len(P)).astype(np.uint32)
-    rj = rng.integers(0, n, len(P)).astype(np.uint32)
+    # non-neighbours: random pairs outside eps
+    ri = rng.integers(0, n, 3 * len(P))
+    rj = rng.integers(0, n, 3 * len(P))
+    Xn = X / np.linalg.norm(X, axis=1, keepdims=True)
+    far = (ri != rj) & (1.0 - np.einsum("ij,ij->i", Xn[ri], Xn[rj]) > eps)
+    ri, rj = ri[far][:len(P)].astype(np.uint32), rj[far][:len(P)].astype(np.uint32)
     pi = np.concatenate([(P >> np.uint64(32)).astype(np.uint32), ri])
     pj = np.concatenate([(P & np.uint64(0xFFFFFFFF)).astype(np.uint32), rj])
-    lab = np.concatenate([np.ones(len(P), np.uint8), np.zeros(len(P), np.uint8)])
+    lab = np.concatenate([np.ones(len(P), np.uint8), np.zeros(len(ri), np.uint8)])
     net = msm.MLPProjection(128, 512, 128, seed=1)
     # neighbours sit at cos ~0.99 in x: m_pos above that pulls them tighter
-    hist = net.train(Xg, _t(pi.view(np.int32)), _t(pj.view(np.int32)), _t(lab), steps=300,
-                     batch=4096, lr=2e-3, m_pos=0.999, m_neg=0.2)
-    assert np.mean(hist[-20:]) < 0.5 * np.mean(hist[:5])
+    hist = net.train(Xg, _t(pi.view(np.int32)), _t(pj.view(np.int32)), _t(lab), steps=1000,
+                     batch=4096, lr=1e-2, m_pos=0.999, m_neg=0.2)
+    assert np.mean(hist[-20:]) < np.mean(hist[:5])
     Y = net.features(Xg)
     miss = {}
     for name, kw in [("random", {}), ("learned", {"Y": Y})]:
@@ -152,7 +156,7 @@ def test_learned_projection_lowers_missing_ratio(msm):
             ratios.append((truth - p.numel()) / truth)
         miss[name] = float(np.mean(ratios))
     assert miss["random"] > 0.01
-    assert miss["learned"] < 0.5 * miss["random"], miss
+    assert miss["learned"] < 0.1 * miss["random"], miss
     # no false pairs with learned strings either
     p, d, _ = msm.eps_graph(Xg, "cosine", eps, wl.ell, wl.k, wl.d, Q=1, seed=21, Y=Y)
     assert p.numel() <= truth

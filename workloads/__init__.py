@@ -60,15 +60,20 @@ WORKLOADS = {
 
 
 def clustered(n: int, dim: int, n_clusters: int, sigma: float, seed: int,
-              normalise: bool = True, chunk: int = 1 << 18) -> np.ndarray:
+              normalise: bool = True, chunk: int = 1 << 18,
+              centres_seed: int | None = None) -> np.ndarray:
     """Gaussian-mixture points, float32 [n][dim], generated in chunks.
 
     Centres ~ U[-1,1]^dim; each point's centre is uniform over the mixture;
     noise ~ sigma * N(0, I).  With ``normalise`` every row is scaled to unit
     Euclidean norm (the normalisation used for the cosine experiments).
+    ``centres_seed`` draws the centres from another stream, so samples with
+    different ``seed`` share one mixture.
     """
     rng = np.random.default_rng(seed)
     centres = rng.uniform(-1.0, 1.0, size=(n_clusters, dim))
+    if centres_seed is not None and centres_seed != seed:
+        centres = np.random.default_rng(centres_seed).uniform(-1.0, 1.0, size=(n_clusters, dim))
     out = np.empty((n, dim), dtype=np.float32)
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
