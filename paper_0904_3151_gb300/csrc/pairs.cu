@@ -589,7 +589,16 @@ __global__ void __launch_bounds__(kThreads)
 check_fields_kernel(CheckArgs a, const uint32_t* fields) {
   __shared__ __align__(16) uint32_t sm_f[kThreads / 32][32][FP];
   __shared__ uint32_t sm_i[kThreads / 32][32];
+  // pair p of a group of <= 32 items, column by column: p = b(b-1)/2 + a
+  __shared__ uint8_t tri_a[496], tri_b[496];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int p = threadIdx.x; p < 496; p += kThreads) {
+    int b = 1;
+    while ((b + 1) * b / 2 <= p) ++b;
+    tri_a[p] = (uint8_t)(p - b * (b - 1) / 2);
+    tri_b[p] = (uint8_t)b;
+  }
+  __syncthreads();
   const uint64_t total = *a.total_work;
   const uint32_t G = *a.ngroups;
   if (total == 0 || G == 0) return;
@@ -651,10 +660,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
         bool pass = false;
         uint32_t ii = 0, jj = 0;
         if (p < P) {
-          int b = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
-          while (b * (b - 1) / 2 > p) --b;
-          while ((b + 1) * b / 2 <= p) ++b;
-          const int aa = p - b * (b - 1) / 2;
+          const int aa = tri_a[p], b = tri_b[p];
           uint32_t fa[FP];
 #pragma unroll
           for (int w = 0; w < FP; ++w) fa[w] = sm_f[warp][aa][w];
@@ -716,16 +722,24 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
       }
       __syncwarp();
       const uint32_t ncols = min(32u, len - (uint32_t)(J * 32));
-      // columns this lane may pair with: in range, and right of the
-      // diagonal on a diagonal tile
-      uint32_t valid = ncols == 32 ? 0xffffffffu : ((1u << ncols) - 1u);
-      if (I == J) valid &= (lane == 31) ? 0u : (0xffffffffu << (lane + 1));
-      if (!va) valid = 0;
+      const uint32_t colmask = ncols == 32 ? 0xffffffffu : ((1u << ncols) - 1u);
       uint32_t gpass = 0;
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c)
-        gpass |= (uint32_t)gaps_differ<FP, FU>(fa, sm_f[warp][c], gapf) << c;
-      gpass &= valid;
+      if (I == J) {
+        // Diagonal tile: round robin -- in step s lane l pairs with column
+        // (l + s) mod 32; steps 1..15 and the lower half of step 16 cover
+        // every unordered pair of the block exactly once with all lanes busy.
+#pragma unroll 4
+        for (int s = 1; s <= 16; ++s) {
+          const int c = (lane + s) & 31;
+          const bool ok = (s < 16 || lane < 16) && gaps_differ<FP, FU>(fa, sm_f[warp][c], gapf);
+          gpass |= (uint32_t)ok << c;
+        }
+      } else {
+#pragma unroll 4
+        for (uint32_t c = 0; c < ncols; ++c)
+          gpass |= (uint32_t)gaps_differ<FP, FU>(fa, sm_f[warp][c], gapf) << c;
+      }
+      gpass &= va ? colmask : 0u;
       uint32_t passm = 0;
       while (gpass) {
         const int c = __ffs(gpass) - 1;
