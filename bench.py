@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--no-missing", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the bf16 and learned-projection forms")
+                    help="skip the bf16, learned-projection and batched forms")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
     return ap.parse_args()
 
 
@@ -138,6 +139,63 @@ def run_forms(msm, wl, X, Xh, n, Q, seed, truth, ratio_plain, ms_plain, steps, s
     else:
         forms["learned"] = {"Q_ladder": ladder, "note": "no Q <= plain Q reached the plain ratio"}
     return forms
+
+
+def run_batched(msm, steps, stream):
+    """Batched form: 256 independent point sets (sizes log-uniform in
+    [1e3, 2e5], dim 96, 20 clusters each, cosine eps 0.12, l=64, k=8, d=4),
+    count-only output.  Plain form: one msm_eps_graph call per set.  Batched
+    form: one graph-captured plan over all sets, launch knobs from the
+    autotuner.  Both draw R from the same seed (identical strings), so their
+    counts, and missing-edge ratios, are identical; Q is the smallest from 7
+    up whose measured ratio is <= 1e-6."""
+    import tempfile
+
+    import torch
+    wl = W.WORKLOADS["batched"]
+    sizes = W.set_sizes(wl.n_sets, wl.set_min, wl.set_max, wl.data_seed)
+    Xh, off = W.clustered_sets(sizes, wl.dim, wl.n_clusters, wl.sigma, wl.data_seed)
+    X = torch.from_numpy(Xh).cuda()
+    del Xh
+    n = int(off[-1])
+    S = len(sizes)
+    truth = np.array([msm.eps_count_exhaustive(X[int(off[s]):int(off[s + 1])], msm.COSINE, wl.eps)
+                      for s in range(S)])
+    T = int(truth.sum())
+    cache = os.path.join(tempfile.gettempdir(), "msm_autotune.txt")
+    for Q in (7, 8, 9):
+        tu = msm.autotune(X, off, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=Q, seed=wl.r_seed,
+                          cache_path=cache)
+        plan = msm.Plan(off, wl.dim, torch.float32, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=Q,
+                        seed=wl.r_seed, tuning=tu)
+        plan.run(X)
+        c, counts, _ = plan.run(X)
+        if (T - c) / T <= 1e-6:
+            break
+        plan.close()
+    ms_b, (cb, counts_b, st) = time_steps(lambda: plan.run(X), steps, stream)
+    graph = plan.is_graph
+    plan.close()
+
+    def step_plain():
+        cs = np.zeros(S, dtype=np.int64)
+        for s in range(S):
+            a, b = int(off[s]), int(off[s + 1])
+            _, _, st2 = msm.eps_graph(X[a:b], msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=Q,
+                                      seed=wl.r_seed, out_mode=msm.OUT_COUNT)
+            cs[s] = st2["count"]
+        return cs
+    step_plain()
+    ms_p, counts_p = time_steps(step_plain, max(1, steps // 2), stream)
+    return {
+        "value": n / (ms_b / 1000.0), "unit": UNIT, "ms_per_step": ms_b, "Q": Q,
+        "missing_ratio": (T - cb) / T, "pairs": cb, "points": n, "sets": S,
+        "per_set_counts_equal_plain": bool(np.array_equal(counts_b, counts_p)),
+        "plain": {"value": n / (ms_p / 1000.0), "ms_per_step": ms_p,
+                  "note": "one msm_eps_graph call (count-only) per set"},
+        "speedup_vs_plain": ms_p / ms_b, "tuning": tu, "cuda_graph": graph,
+        "note": "all sets and groupings in one captured CUDA graph per step (radix segments "
+                "split at set boundaries, eps test fused into the pair check)"}
 
 
 def workload_desc(wl, n, Q):
@@ -453,6 +511,8 @@ def main():
     if rank == 0 and world == 1 and not a.no_forms and missing is not None:
         forms = run_forms(msm, wl, X, Xh, n, Q, seed, missing["truth_pairs"], missing["ratio"],
                           ms, max(2, min(3, a.steps)), stream)
+        if not a.no_batched:
+            forms["batched"] = run_batched(msm, max(2, min(3, a.steps)), stream)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
     cpu = None

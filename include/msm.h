@@ -113,7 +113,9 @@ typedef struct msm_params {
   int out_mode;      /* MSM_OUT_*                                       */
   int flags;         /* MSM_FLAG_*                                      */
   int group_bits;    /* grouping-key width 8..32; 0 = automatic         */
-  int reserved;
+  int check_min_blocks; /* tuning: register budget of the count-only pair
+                           check, as resident CTAs per SM: 2, 4 or 5;
+                           0 = automatic                                  */
   int64_t cand_capacity; /* initial candidate buffer (pairs); 0 = auto */
   /* Optional projection features (learned form): when Y is non-NULL the
    * strings are the sign projection of Y (device [n][dim_y] of dtype_y)
@@ -121,6 +123,9 @@ typedef struct msm_params {
   const void* Y;
   int dim_y;
   int dtype_y;
+  /* Tuning (results never depend on these; 0 = automatic): */
+  int masks_per_batch;   /* kept-block sets grouped per sort batch         */
+  int check_ctas_per_sm; /* pair-check grid, CTAs per SM (1..16)           */
 } msm_params;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -239,6 +244,90 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
                   float eps, double miss_ratio, const msm_params* params,
                   const msm_allocator* alloc, msm_pairs* out,
                   msm_stats* stats, void* stream);
+
+/* ---- Batched form: many independent point sets in one call ----
+ * The paper builds one graph per call.  These entry points run the same
+ * method on S independent point sets at once: set s is the rows
+ * [set_offsets[s], set_offsets[s+1]) of one concatenated pool, and pairs
+ * are only formed inside a set (no set sees another).  Every grouping sort
+ * covers all sets (one radix segment per kept-block set, split at the set
+ * boundaries), so the launch count does not grow with S.
+ *   set_offsets  host [nsets + 1]: set_offsets[0] = 0, nondecreasing; the
+ *                pool has n = set_offsets[nsets] rows (2 <= n < 2^31);
+ *                empty and one-point sets are allowed; 1 <= nsets <= 2^24
+ * Pair indices are rows of the concatenated pool. */
+
+/* msm_enumerate over the sets: every pair (i, j), i < j, of one set whose
+ * strings lie within Hamming distance d in at least one pool.  Strings are
+ * [Q][n][W] over the concatenated rows.  Synchronises. */
+int msm_enumerate_sets(const uint64_t* strings, const int64_t* set_offsets,
+                       int nsets, int ell, int k, int d, int Q, int flags,
+                       const msm_allocator* alloc, msm_pairs* out,
+                       msm_stats* stats, void* stream);
+
+/* msm_eps_graph over the sets (X: host or device [n][dim] of dtype, the
+ * concatenated rows).  set_counts: optional host [nsets], receives the
+ * number of result pairs of every set.  With MSM_OUT_COUNT no pair or
+ * candidate list is stored: each candidate is checked against eps as soon
+ * as the pair check finds it.  Synchronises. */
+int msm_eps_graph_sets(const void* X, const int64_t* set_offsets, int nsets,
+                       int dim, int dtype, int metric, float eps,
+                       double miss_ratio, const msm_params* params,
+                       const msm_allocator* alloc, msm_pairs* out,
+                       int64_t* set_counts, msm_stats* stats, void* stream);
+
+/* ---- Reusable count-only plans (batched form, CUDA graph) ----
+ * A plan fixes the shape of msm_eps_graph_sets with MSM_OUT_COUNT: the set
+ * offsets, dim, dtype, metric, eps and msm_params (Y must be NULL; a given R
+ * must stay alive and unchanged while the plan exists).  msm_plan_run then
+ * builds the graph counts of any X of that shape.  The whole pipeline
+ * (norms, projection, every grouping sort and pair check of every
+ * replicate, with the epsilon test fused into the pair check) is issued
+ * without a host round trip; the first run executes it directly and keeps
+ * its buffers, the second captures it into a CUDA graph, and every later run
+ * is a single graph launch plus one read-back of the counts.  Results equal
+ * those of msm_eps_graph_sets. */
+typedef struct msm_plan msm_plan;
+
+/* Creates a plan (device memory from `alloc`, or cudaMallocAsync when NULL;
+ * the allocator must outlive the plan).  *plan receives the handle. */
+int msm_plan_create(const int64_t* set_offsets, int nsets, int dim, int dtype,
+                    int metric, float eps, double miss_ratio,
+                    const msm_params* params, const msm_allocator* alloc,
+                    msm_plan** plan);
+
+/* Device buffer [n][dim] of the plan's dtype that every run reads; filling
+ * it directly and passing X = NULL (or this pointer) avoids a copy. */
+void* msm_plan_input(msm_plan* plan);
+
+/* One run.  X: host or device [n][dim] (copied into the plan's input), or
+ * NULL to use the input buffer as it is.  *count receives the number of
+ * result pairs, set_counts (optional host [nsets]) the number per set,
+ * stats (optional) the counters and ms[7] the device time of the run.
+ * Ordered after prior work on `stream`; synchronises on the plan.  When the
+ * tensor-core projection cannot settle every sign from its queue, the call
+ * is answered on the CUDA-core projection and the plan is rebuilt on it. */
+int msm_plan_run(msm_plan* plan, const void* X, int64_t* count,
+                 int64_t* set_counts, msm_stats* stats, void* stream);
+
+/* 1 once the plan runs as a captured CUDA graph (from its second run on). */
+int msm_plan_is_graph(const msm_plan* plan);
+
+/* Releases the plan and its device memory (synchronises on the plan). */
+void msm_plan_destroy(msm_plan* plan, void* stream);
+
+/* Autotuner for count-only runs of one shape (msm_eps_graph_sets or a
+ * plan): times candidate values of the launch knobs of msm_params
+ * (check_min_blocks, check_ctas_per_sm, masks_per_batch) on X (device or
+ * host [n][dim]) with at most 2 replicates per trial, and writes the fastest
+ * into *params.  With cache_path (or NULL), a result stored there for the
+ * same device, shape and geometry is used without timing, and a new result
+ * is appended to the file.  Results never depend on the knobs.
+ * Synchronises. */
+int msm_autotune(const void* X, const int64_t* set_offsets, int nsets,
+                 int dim, int dtype, int metric, float eps,
+                 msm_params* params, const char* cache_path,
+                 const msm_allocator* alloc, void* stream);
 
 /* ---- Learned projection ----
  * Sec. 6 of the paper proposes combining MSM with non-random hashing.  The

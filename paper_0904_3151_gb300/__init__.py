@@ -11,13 +11,15 @@ from __future__ import annotations
 import ctypes
 import traceback
 
+import numpy as np
 import torch
 
 from . import _lib
 from ._lib import Allocator, Pairs, Params, Stats
 
 __all__ = ["MSMError", "gaussian", "project", "enumerate_pairs", "recheck",
-           "eps_graph", "eps_count_exhaustive", "collision_p", "miss_bound",
+           "eps_graph", "enumerate_sets", "eps_graph_sets", "Plan", "autotune",
+           "eps_count_exhaustive", "collision_p", "miss_bound",
            "solve_Q", "unpack_pairs", "COSINE", "EUCLIDEAN", "lib"]
 
 COSINE, EUCLIDEAN = 0, 1
@@ -155,18 +157,8 @@ def recheck(X: torch.Tensor, cand: torch.Tensor, metric, eps: float):
     return pairs[:cnt.value], dist[:cnt.value], rec.value
 
 
-def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
-              Q: int = 0, miss_ratio: float = 1e-6, R: torch.Tensor | None = None,
-              seed: int = 0, out_mode: int = OUT_PAIRS_DIST, canonical: bool = False,
-              group_bits: int = 0, cand_capacity: int = 0, simt_projection: bool = False,
-              Y: torch.Tensor | None = None, device=None):
-    """The whole method.  X may be a CUDA tensor or a (pinned) CPU tensor,
-    which the library copies in.  With Y (CUDA [n][dim_y], e.g. learned
-    features) the strings come from Y while the recheck uses X.
-    Returns (pairs, dist, stats)."""
-    assert X.is_contiguous() and X.dim() == 2
-    n, dim = X.shape
-    dev = X.device if X.is_cuda else torch.device(device or "cuda")
+def _params(ell, k, d, Q, seed, R, Y, n, out_mode, canonical, simt_projection, group_bits,
+            cand_capacity, tuning=None):
     p = Params()
     p.ell, p.k, p.d, p.Q = ell, k, d, Q
     p.seed = seed
@@ -178,6 +170,28 @@ def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
     p.flags = (FLAG_CANONICAL if canonical else 0) | (FLAG_SIMT_PROJECTION if simt_projection else 0)
     p.group_bits = group_bits
     p.cand_capacity = cand_capacity
+    for key, v in (tuning or {}).items():
+        assert key in ("masks_per_batch", "check_ctas_per_sm", "check_min_blocks"), key
+        setattr(p, key, int(v))
+    return p
+
+
+def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
+              Q: int = 0, miss_ratio: float = 1e-6, R: torch.Tensor | None = None,
+              seed: int = 0, out_mode: int = OUT_PAIRS_DIST, canonical: bool = False,
+              group_bits: int = 0, cand_capacity: int = 0, simt_projection: bool = False,
+              Y: torch.Tensor | None = None, device=None, tuning: dict | None = None):
+    """The whole method.  X may be a CUDA tensor or a (pinned) CPU tensor,
+    which the library copies in.  With Y (CUDA [n][dim_y], e.g. learned
+    features) the strings come from Y while the recheck uses X.  ``tuning``
+    sets launch knobs of msm_params (masks_per_batch, check_ctas_per_sm,
+    check_min_blocks); results do not depend on them.
+    Returns (pairs, dist, stats)."""
+    assert X.is_contiguous() and X.dim() == 2
+    n, dim = X.shape
+    dev = X.device if X.is_cuda else torch.device(device or "cuda")
+    p = _params(ell, k, d, Q, seed, R, Y, n, out_mode, canonical, simt_projection, group_bits,
+                cand_capacity, tuning)
     A = _TorchAllocator(dev)
     out = Pairs()
     st = Stats()
@@ -191,6 +205,146 @@ def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
     s = st.as_dict()
     s["count"] = int(out.count)
     return pairs, dist, s
+
+
+def _offsets(set_offsets):
+    off = np.ascontiguousarray(np.asarray(set_offsets, dtype=np.int64))
+    assert off.ndim == 1 and off.size >= 2
+    return off, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), off.size - 1
+
+
+def enumerate_sets(strings: torch.Tensor, set_offsets, ell: int, k: int, d: int,
+                   canonical: bool = False):
+    """enumerate_pairs over independent point sets: set s is rows
+    [set_offsets[s], set_offsets[s+1]) of the pool; pairs never cross sets.
+    Returns (pairs, stats)."""
+    assert strings.is_cuda and strings.is_contiguous() and strings.dim() == 3
+    Q, n, W = strings.shape
+    off, offp, S = _offsets(set_offsets)
+    assert off[-1] == n and W == (ell + 63) // 64
+    A = _TorchAllocator(strings.device)
+    out = Pairs()
+    st = Stats()
+    _check(lib().msm_enumerate_sets(ctypes.c_void_p(strings.data_ptr()), offp, S, ell, k, d, Q,
+                                    FLAG_CANONICAL if canonical else 0, ctypes.byref(A.struct),
+                                    ctypes.byref(out), ctypes.byref(st), _stream()),
+           "msm_enumerate_sets")
+    return A.take(out.pairs, out.count, torch.int64), st.as_dict()
+
+
+def eps_graph_sets(X: torch.Tensor, set_offsets, metric, eps: float, ell: int, k: int, d: int,
+                   Q: int = 0, miss_ratio: float = 1e-6, R: torch.Tensor | None = None,
+                   seed: int = 0, out_mode: int = OUT_COUNT, canonical: bool = False,
+                   group_bits: int = 0, cand_capacity: int = 0, simt_projection: bool = False,
+                   device=None, tuning: dict | None = None):
+    """eps_graph over independent point sets (rows [set_offsets[s],
+    set_offsets[s+1]) of X form set s).  Returns (pairs, dist, set_counts,
+    stats); set_counts is a numpy int64 [S] of result pairs per set.  The
+    default output mode is count-only, which stores no pair list."""
+    assert X.is_contiguous() and X.dim() == 2
+    n, dim = X.shape
+    off, offp, S = _offsets(set_offsets)
+    assert off[-1] == n
+    dev = X.device if X.is_cuda else torch.device(device or "cuda")
+    p = _params(ell, k, d, Q, seed, R, None, n, out_mode, canonical, simt_projection, group_bits,
+                cand_capacity, tuning)
+    counts = np.zeros(S, dtype=np.int64)
+    A = _TorchAllocator(dev)
+    out = Pairs()
+    st = Stats()
+    with torch.cuda.device(dev):
+        _check(lib().msm_eps_graph_sets(
+            ctypes.c_void_p(X.data_ptr()), offp, S, dim, _dtype(X), _metric(metric),
+            ctypes.c_float(eps), ctypes.c_double(miss_ratio), ctypes.byref(p),
+            ctypes.byref(A.struct), ctypes.byref(out),
+            counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(st), _stream()),
+            "msm_eps_graph_sets")
+    pairs = A.take(out.pairs, out.count, torch.int64) if out_mode != OUT_COUNT else None
+    dist = A.take(out.dist, out.count, torch.float32) if out_mode == OUT_PAIRS_DIST else None
+    s = st.as_dict()
+    s["count"] = int(out.count)
+    return pairs, dist, counts, s
+
+
+def autotune(X: torch.Tensor, set_offsets, metric, eps: float, ell: int, k: int, d: int,
+             Q: int, seed: int = 0, R: torch.Tensor | None = None, cache_path: str | None = None,
+             simt_projection: bool = False) -> dict:
+    """msm_autotune: the fastest launch knobs for count-only runs of this
+    shape (timed on X; cached per device and shape in ``cache_path``).
+    Returns the ``tuning`` dict for eps_graph / eps_graph_sets / Plan."""
+    assert X.is_contiguous() and X.dim() == 2
+    n, dim = X.shape
+    off, offp, S = _offsets(set_offsets if set_offsets is not None else [0, n])
+    assert off[-1] == n
+    p = _params(ell, k, d, Q, seed, R, None, n, OUT_COUNT, False, simt_projection, 0, 0)
+    A = _TorchAllocator(X.device if X.is_cuda else torch.device("cuda"))
+    _check(lib().msm_autotune(ctypes.c_void_p(X.data_ptr()), offp, S, dim, _dtype(X),
+                              _metric(metric), ctypes.c_float(eps), ctypes.byref(p),
+                              cache_path.encode() if cache_path else None,
+                              ctypes.byref(A.struct), _stream()), "msm_autotune")
+    return {"check_min_blocks": p.check_min_blocks, "check_ctas_per_sm": p.check_ctas_per_sm,
+            "masks_per_batch": p.masks_per_batch}
+
+
+class Plan:
+    """msm_plan: a reusable count-only run of eps_graph_sets for inputs of
+    one shape.  The first run executes directly, the second captures a CUDA
+    graph, later runs are one graph launch each.  ``input`` is the device
+    buffer the plan reads (fill it and call run() without X to skip a copy)."""
+
+    def __init__(self, set_offsets, dim: int, dtype, metric, eps: float, ell: int, k: int,
+                 d: int, Q: int, seed: int = 0, R: torch.Tensor | None = None,
+                 miss_ratio: float = 1e-6, simt_projection: bool = False,
+                 tuning: dict | None = None, device=None):
+        self.off, offp, self.S = _offsets(set_offsets)
+        self.n, self.dim = int(self.off[-1]), dim
+        self.dtype = dtype
+        self.device = torch.device(device or "cuda")
+        self._R = R
+        p = _params(ell, k, d, Q, seed, R, None, self.n, OUT_COUNT, False, simt_projection, 0, 0,
+                    tuning)
+        self._A = _TorchAllocator(self.device)
+        h = ctypes.c_void_p()
+        dt = DT_BF16 if dtype == torch.bfloat16 else DT_F32
+        with torch.cuda.device(self.device):
+            _check(lib().msm_plan_create(offp, self.S, dim, dt, _metric(metric),
+                                         ctypes.c_float(eps), ctypes.c_double(miss_ratio),
+                                         ctypes.byref(p), ctypes.byref(self._A.struct),
+                                         ctypes.byref(h)), "msm_plan_create")
+        self._h = h
+        ptr = lib().msm_plan_input(h)
+        self.input = self._A.live[ptr].view(dtype)[: self.n * dim].view(self.n, dim)
+
+    def run(self, X: torch.Tensor | None = None):
+        """Returns (count, set_counts numpy int64 [S], stats)."""
+        cnt = ctypes.c_int64(0)
+        counts = np.zeros(self.S, dtype=np.int64)
+        st = Stats()
+        if X is not None:
+            assert X.is_contiguous() and tuple(X.shape) == (self.n, self.dim) and X.dtype == self.dtype
+        with torch.cuda.device(self.device):
+            _check(lib().msm_plan_run(self._h, ctypes.c_void_p(X.data_ptr()) if X is not None else None,
+                                      ctypes.byref(cnt),
+                                      counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      ctypes.byref(st), _stream()), "msm_plan_run")
+        s = st.as_dict()
+        s["count"] = int(cnt.value)
+        return int(cnt.value), counts, s
+
+    @property
+    def is_graph(self) -> bool:
+        return bool(lib().msm_plan_is_graph(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().msm_plan_destroy(self._h, None)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
 
 
 class MLPProjection:

@@ -51,9 +51,10 @@ class Stats(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_int), ("k", ctypes.c_int), ("d", ctypes.c_int), ("Q", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("R", ctypes.c_void_p), ("out_mode", ctypes.c_int),
-                ("flags", ctypes.c_int), ("group_bits", ctypes.c_int), ("reserved", ctypes.c_int),
-                ("cand_capacity", ctypes.c_int64), ("Y", ctypes.c_void_p), ("dim_y", ctypes.c_int),
-                ("dtype_y", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("group_bits", ctypes.c_int),
+                ("check_min_blocks", ctypes.c_int), ("cand_capacity", ctypes.c_int64),
+                ("Y", ctypes.c_void_p), ("dim_y", ctypes.c_int), ("dtype_y", ctypes.c_int),
+                ("masks_per_batch", ctypes.c_int), ("check_ctas_per_sm", ctypes.c_int)]
 
 
 # Every symbol include/msm.h declares, with its ctypes signature.
@@ -81,6 +82,25 @@ SIGNATURES = {
                                      ctypes.c_float, ctypes.c_double, ctypes.POINTER(Params),
                                      ctypes.POINTER(Allocator), ctypes.POINTER(Pairs),
                                      ctypes.POINTER(Stats), vp]),
+    "msm_enumerate_sets": (ctypes.c_int, [vp, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(Allocator), ctypes.POINTER(Pairs),
+                                          ctypes.POINTER(Stats), vp]),
+    "msm_eps_graph_sets": (ctypes.c_int, [vp, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_float, ctypes.c_double,
+                                          ctypes.POINTER(Params), ctypes.POINTER(Allocator),
+                                          ctypes.POINTER(Pairs), i64p, ctypes.POINTER(Stats), vp]),
+    "msm_plan_create": (ctypes.c_int, [i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_float, ctypes.c_double,
+                                       ctypes.POINTER(Params), ctypes.POINTER(Allocator),
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "msm_plan_input": (ctypes.c_void_p, [vp]),
+    "msm_plan_run": (ctypes.c_int, [vp, vp, i64p, i64p, ctypes.POINTER(Stats), vp]),
+    "msm_plan_is_graph": (ctypes.c_int, [vp]),
+    "msm_plan_destroy": (None, [vp, vp]),
+    "msm_autotune": (ctypes.c_int, [vp, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_float, ctypes.POINTER(Params),
+                                    ctypes.c_char_p, ctypes.POINTER(Allocator), vp]),
     "msm_free_pairs": (None, [ctypes.POINTER(Pairs), ctypes.POINTER(Allocator), vp]),
     "msm_mlp_forward": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, vp, vp,
                                        vp, ctypes.c_int, ctypes.c_int, vp, vp]),

@@ -8,7 +8,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <functional>
 #include <vector>
 
 #include "msm_internal.cuh"
@@ -138,6 +137,25 @@ Scratch::~Scratch() {
 }
 
 void* Scratch::get(size_t bytes) {
+  if (log_ && replay_) {
+    if (log_->next >= log_->count || log_->bytes[log_->next] != bytes) {
+      set_error("plan replay requested a buffer the recorded run did not");
+      return nullptr;
+    }
+    return log_->ptr[log_->next++];
+  }
+  if (log_) {
+    if (log_->count >= 128) {
+      set_error("too many plan buffers");
+      return nullptr;
+    }
+    void* p = raw_alloc(a_, bytes, s_);
+    if (p) {
+      log_->ptr[log_->count] = p;
+      log_->bytes[log_->count++] = bytes;
+    }
+    return p;
+  }
   if (nlive_ >= 64) {
     set_error("too many scratch buffers");
     return nullptr;
@@ -148,6 +166,7 @@ void* Scratch::get(size_t bytes) {
 }
 
 void Scratch::put(void* p) {
+  if (log_) return;
   for (int i = 0; i < nlive_; ++i)
     if (live_[i] == p) {
       raw_free(a_, p, s_);
@@ -157,6 +176,7 @@ void Scratch::put(void* p) {
 }
 
 void Scratch::release(void* p) {
+  if (log_) return;
   for (int i = 0; i < nlive_; ++i)
     if (live_[i] == p) {
       live_[i] = live_[--nlive_];
@@ -256,18 +276,94 @@ static int read_back(T* host, const T* dev, cudaStream_t s) {
   return MSM_OK;
 }
 
+// Device set table for the host offsets off[0..S] (validated by the caller:
+// off[0] = 0, nondecreasing, off[S] = n).  One set keeps the defaults.
+static int make_set_table(Scratch& sc, const int64_t* off, int S, int64_t n, SetTable* t) {
+  *t = SetTable();
+  if (S <= 1) return MSM_OK;
+  cudaStream_t s = sc.stream();
+  const int64_t tile = group_tile_items();
+  std::vector<int> set_tile0((size_t)S + 1), tile_set;
+  for (int j = 0; j < S; ++j) {
+    set_tile0[j] = (int)tile_set.size();
+    const int64_t tiles = (off[j + 1] - off[j] + tile - 1) / tile;
+    for (int64_t i = 0; i < tiles; ++i) tile_set.push_back(j);
+  }
+  set_tile0[S] = (int)tile_set.size();
+  std::vector<uint32_t> bits((size_t)((n + 31) / 32), 0u);
+  for (int j = 1; j < S; ++j)
+    if (off[j] < n) bits[(size_t)(off[j] >> 5)] |= 1u << (off[j] & 31);
+  const size_t T = tile_set.size();
+  int64_t* off_d = (int64_t*)sc.get(8 * ((size_t)S + 1));
+  int* ts_d = (int*)sc.get(4 * (T > 0 ? T : 1));
+  int* st0_d = (int*)sc.get(4 * ((size_t)S + 1));
+  uint32_t* bits_d = (uint32_t*)sc.get(4 * bits.size());
+  if (!off_d || !ts_d || !st0_d || !bits_d) return MSM_E_NOMEM;
+  if (!sc.replaying()) {  // a replayed plan's buffers already hold the table
+    MSM_CUDA(cudaMemcpyAsync(off_d, off, 8 * ((size_t)S + 1), cudaMemcpyHostToDevice, s));
+    if (T) MSM_CUDA(cudaMemcpyAsync(ts_d, tile_set.data(), 4 * T, cudaMemcpyHostToDevice, s));
+    MSM_CUDA(cudaMemcpyAsync(st0_d, set_tile0.data(), 4 * ((size_t)S + 1), cudaMemcpyHostToDevice, s));
+    MSM_CUDA(cudaMemcpyAsync(bits_d, bits.data(), 4 * bits.size(), cudaMemcpyHostToDevice, s));
+    // the host vectors die on return: make sure the copies have read them
+    MSM_CUDA(cudaStreamSynchronize(s));
+  }
+  t->S = S;
+  t->off = off_d;
+  t->tile_set = ts_d;
+  t->set_tile0 = st0_d;
+  t->start_bits = bits_d;
+  t->T = (int)T;
+  return MSM_OK;
+}
+
+static int check_sets(const int64_t* off, int S, int64_t* n) {
+  if (!off || S < 1 || S > (1 << 24)) return set_error("need 1 <= nsets <= 2^24 and set offsets"), MSM_E_INVAL;
+  if (off[0] != 0) return set_error("set_offsets[0] must be 0"), MSM_E_INVAL;
+  for (int j = 0; j < S; ++j)
+    if (off[j + 1] < off[j]) return set_error("set_offsets must be nondecreasing"), MSM_E_INVAL;
+  *n = off[S];
+  return MSM_OK;
+}
+
+// Count-only recheck fused into the pair check (X == NULL: not fused).
+struct FuseCfg {
+  const void* X = nullptr;
+  int dtype = 0, dim = 0, metric = 0;
+  float eps = 0.f;
+  const float* nrm = nullptr;
+  unsigned long long* kept = nullptr;      // [0] within eps, [1] double decisions
+  unsigned long long* set_kept = nullptr;  // per set (or NULL)
+};
+
 // A3-A7 over all replicates.  On success *cand (allocated from sc, owned by
-// sc) holds *count candidate pairs.
-// With a sink, every mask batch's candidates are handed to it (device
-// pointer, count) and the buffer restarts empty, so memory is bounded by one
-// batch; *count_out is then 0 and stats->cand the total handed over.
-using CandSink = std::function<int(const uint64_t*, int64_t)>;
+// sc) holds *count candidate pairs.  Fused (fz.X set): no candidate list is
+// kept; each candidate is rechecked inside the pair check and counted in
+// fz.kept (and per set in fz.set_kept); *cand_out is NULL, *count_out 0.
+// Launch tuning of run_msm (0 = automatic); results never depend on it.
+struct Tuning {
+  int group_bits = 0;
+  int masks_per_batch = 0;
+  int check_ctas_per_sm = 0;
+  int check_min_blocks = 0;
+};
+
+static Tuning tuning_of(const msm_params* p) {
+  Tuning t;
+  t.group_bits = p->group_bits;
+  t.masks_per_batch = p->masks_per_batch;
+  t.check_ctas_per_sm = p->check_ctas_per_sm;
+  t.check_min_blocks = p->check_min_blocks;
+  return t;
+}
 
 static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
-                   int k, int d, int Q, int group_bits_req, int64_t cap0,
+                   int k, int d, int Q, const Tuning& tu, int64_t cap0,
                    uint64_t** cand_out, int64_t* count_out, msm_stats* st,
-                   PhaseTimer& tm, const CandSink& sink = CandSink()) {
+                   PhaseTimer& tm, const SetTable& sets = SetTable(),
+                   const FuseCfg& fz = FuseCfg(),
+                   unsigned long long** counters_out = nullptr) {
   cudaStream_t s = sc.stream();
+  const bool fused = fz.X != nullptr;
   int64_t total_cand = 0;
   const BlockLayout L = make_layout(ell, k);
   std::vector<MaskDesc> masks = make_masks(L, d);
@@ -285,7 +381,7 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
   // a 24-bit mix (3 radix passes) while n <= 2^23, beyond that 32 bits.
   // A mixed key lets unequal K blocks share a key for ~n^2 / 2^(bits+1)
   // pairs per grouping; the in-group test rejects those pairs.
-  int gb = group_bits_req;
+  int gb = tu.group_bits;
   const bool use_sub = gb <= 0 && anygap && maxwidth <= 16;
   if (gb <= 0) {
     if (use_sub) gb = 32;
@@ -301,20 +397,33 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
   const int passes = (gb + 7) / 8;
   const int W = L.W;
 
-  // Masks per batch: bound the grouped items to 2^28.
+  // Masks per batch: bound the grouped items to 2^28 (or as tuned, below
+  // 2^32 items).
   int64_t Sb = ((int64_t)1 << 28) / n;
+  if (tu.masks_per_batch > 0) {
+    Sb = tu.masks_per_batch;
+    if (Sb * n >= ((int64_t)1 << 32)) Sb = (((int64_t)1 << 32) - 1) / n;
+  }
   if (Sb < 1) Sb = 1;
   if (Sb > M) Sb = M;
+  if (tu.check_ctas_per_sm < 0 || tu.check_ctas_per_sm > 16 ||
+      (tu.check_min_blocks != 0 && tu.check_min_blocks != 2 && tu.check_min_blocks != 4 &&
+       tu.check_min_blocks != 5))
+    return set_error("invalid pair-check tuning"), MSM_E_INVAL;
 
   BlockLayout* dL = (BlockLayout*)sc.get(sizeof(BlockLayout));
   MaskDesc* dM = (MaskDesc*)sc.get(sizeof(MaskDesc) * M);
   unsigned long long* counters = (unsigned long long*)sc.get(256);
-  void* gws = sc.get(group_scratch_bytes(n, (int)Sb));
+  void* gws = sc.get(group_scratch_bytes(n, (int)Sb, sets.S));
   void* pws = sc.get(pairs_scratch_bytes(n * Sb));
   if (!dL || !dM || !counters || !gws || !pws) return MSM_E_NOMEM;
-  MSM_CUDA(cudaMemcpyAsync(dL, &L, sizeof(L), cudaMemcpyHostToDevice, s));
-  MSM_CUDA(cudaMemcpyAsync(dM, masks.data(), sizeof(MaskDesc) * M, cudaMemcpyHostToDevice, s));
+  if (!sc.replaying()) {  // a replayed plan's buffers already hold these
+    MSM_CUDA(cudaMemcpyAsync(dL, &L, sizeof(L), cudaMemcpyHostToDevice, s));
+    MSM_CUDA(cudaMemcpyAsync(dM, masks.data(), sizeof(MaskDesc) * M, cudaMemcpyHostToDevice, s));
+    if (sc.sync_free()) MSM_CUDA(cudaStreamSynchronize(s));  // host sources die on return
+  }
   MSM_CUDA(cudaMemsetAsync(counters, 0, 256, s));
+  if (counters_out) *counters_out = counters;
   unsigned long long* count_dev = counters;
   unsigned long long* checks_dev = counters + 1;
 
@@ -328,9 +437,12 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
     if (rc) return rc;
   }
 
-  int64_t cap = cap0 > 0 ? cap0 : 16 * n;
-  uint64_t* cand = (uint64_t*)sc.get(8 * (size_t)cap);
-  if (!cand) return MSM_E_NOMEM;
+  int64_t cap = fused ? 0 : (cap0 > 0 ? cap0 : 16 * n);
+  uint64_t* cand = nullptr;
+  if (!fused) {
+    cand = (uint64_t*)sc.get(8 * (size_t)cap);
+    if (!cand) return MSM_E_NOMEM;
+  }
   int64_t count = 0, retries = 0;
 
   for (int q = 0; q < Q; ++q) {
@@ -346,6 +458,7 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
       gbt.group_bits = gb;
       gbt.passes = passes;
       gbt.layout = dL;
+      gbt.sets = sets;
       uint32_t *keys = nullptr, *vals = nullptr;
       tm.mark(2);
       int rc = run_grouping(gbt, gws, &keys, &vals, s);
@@ -365,9 +478,28 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
       pb.fields = fields;
       pb.FP = FP;
       pb.FU = (k + 1) / 2;
+      pb.start_bits = sets.start_bits;
+      pb.X = fz.X;
+      pb.dtype = fz.dtype;
+      pb.dim = fz.dim;
+      pb.metric = fz.metric;
+      pb.eps = fz.eps;
+      pb.nrm = fz.nrm;
+      pb.kept = fz.kept;
+      pb.set_kept = fz.set_kept;
+      pb.set_off = sets.off;
+      pb.nsets = sets.S;
+      pb.ctas_per_sm = tu.check_ctas_per_sm;
+      pb.min_blocks = tu.check_min_blocks;
       tm.mark(3);
       rc = find_groups(pb, pws, checks_dev, s);
       if (rc) return rc;
+      if (fused) {  // candidates are rechecked and counted in place
+        tm.mark(4);
+        rc = check_groups(pb, pws, nullptr, 0, count_dev, s);
+        if (rc) return rc;
+        continue;
+      }
       while (true) {
         tm.mark(4);
         rc = check_groups(pb, pws, cand, cap, count_dev, s);
@@ -395,17 +527,16 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
         MSM_CUDA(cudaStreamSynchronize(s));
         ++retries;
       }
-      if (sink) {
-        // hand this batch's candidates over and start the next batch empty
-        int rc = sink(cand, count);
-        if (rc) return rc;
-        total_cand += count;
-        count = 0;
-        MSM_CUDA(cudaMemsetAsync(count_dev, 0, sizeof(unsigned long long), s));
-      }
     }
   }
-  if (!sink) total_cand = count;
+  tm.mark(-1);
+  total_cand = count;
+  if (fused && st) {
+    unsigned long long c = 0;
+    int rc = read_back(&c, count_dev, s);
+    if (rc) return rc;
+    total_cand = (int64_t)c;
+  }
   if (st) {
     unsigned long long ch = 0;
     int rc = read_back(&ch, checks_dev, s);
@@ -434,7 +565,8 @@ static size_t dtype_size(int dtype) { return dtype == MSM_DT_BF16 ? 2 : 4; }
 
 // Row norms + input validation.
 static int norms_and_check(Scratch& sc, const void* X, int dtype, int64_t n,
-                           int dim, int metric, double** nrm64, float** nrm32) {
+                           int dim, int metric, double** nrm64, float** nrm32,
+                           unsigned** flags_out = nullptr) {
   cudaStream_t s = sc.stream();
   *nrm64 = (double*)sc.get(8 * (size_t)n);
   *nrm32 = (float*)sc.get(4 * (size_t)n);
@@ -443,6 +575,10 @@ static int norms_and_check(Scratch& sc, const void* X, int dtype, int64_t n,
   MSM_CUDA(cudaMemsetAsync(flags, 0, 4, s));
   int rc = launch_row_norms(X, dtype, n, dim, *nrm64, *nrm32, flags, s);
   if (rc) return rc;
+  if (sc.sync_free()) {  // checked by the plan after the work completes
+    if (flags_out) *flags_out = flags;
+    return MSM_OK;
+  }
   unsigned f = 0;
   rc = read_back(&f, flags, s);
   if (rc) return rc;
@@ -458,7 +594,8 @@ static int norms_and_check(Scratch& sc, const void* X, int dtype, int64_t n,
 static int run_projection(Scratch& sc, const void* X, int dtype, int64_t n,
                           int dim, const float* R, const float* xnorm, int Q,
                           int ell, int flags, uint64_t* strings,
-                          unsigned long long* recompute_dev) {
+                          unsigned long long* recompute_dev,
+                          unsigned** status_out = nullptr) {
   cudaStream_t s = sc.stream();
   bool simt = (flags & MSM_FLAG_SIMT_PROJECTION) != 0 ||
               !tc_project_supported(dtype, dim, (uintptr_t)X);
@@ -467,9 +604,11 @@ static int run_projection(Scratch& sc, const void* X, int dtype, int64_t n,
     unsigned* status = (unsigned*)sc.get(256);
     if (!ws || !status) return MSM_E_NOMEM;
     MSM_CUDA(cudaMemsetAsync(status, 0, 256, s));
+    if (status_out) *status_out = status;
     bool fell_back = false;
     int rc = launch_project_tc(X, dtype, n, dim, R, xnorm, Q, ell, strings,
-                               recompute_dev, ws, status, &fell_back, s);
+                               recompute_dev, ws, status, sc.sync_free() ? nullptr : &fell_back,
+                               s);
     sc.put(ws);
     if (rc) return rc;
     if (!fell_back) return MSM_OK;
@@ -594,10 +733,9 @@ int msm_project(const void* X, int64_t n, int dim, int dtype, const float* R,
   return MSM_OK;
 }
 
-int msm_enumerate(const uint64_t* strings, int64_t n, int ell, int k, int d,
-                  int Q, int flags, const msm_allocator* alloc,
-                  msm_pairs* out, msm_stats* stats, void* stream) {
-  cudaStream_t s = (cudaStream_t)stream;
+static int enumerate_impl(const uint64_t* strings, int64_t n, const int64_t* off, int S,
+                          int ell, int k, int d, int Q, int flags, const msm_allocator* alloc,
+                          msm_pairs* out, msm_stats* stats, cudaStream_t s) {
   if (!strings || !out || Q < 1) return set_error("invalid msm_enumerate arguments"), MSM_E_INVAL;
   int rc = check_geometry(n, ell, k, d);
   if (rc) return rc;
@@ -608,10 +746,13 @@ int msm_enumerate(const uint64_t* strings, int64_t n, int ell, int k, int d,
   Scratch sc(alloc, s);
   PhaseTimer tm(stats != nullptr, s);
   KtScope kts(stats != nullptr);
+  SetTable sets;
+  rc = make_set_table(sc, off, S, n, &sets);
+  if (rc) return rc;
   tm.mark(2);
   uint64_t* cand = nullptr;
   int64_t m = 0;
-  rc = run_msm(sc, strings, n, ell, k, d, Q, 0, 0, &cand, &m, stats, tm);
+  rc = run_msm(sc, strings, n, ell, k, d, Q, Tuning(), 0, &cand, &m, stats, tm, sets);
   if (rc) return rc;
   if ((flags & MSM_FLAG_CANONICAL) && m > 1) {
     tm.mark(6);
@@ -630,6 +771,24 @@ int msm_enumerate(const uint64_t* strings, int64_t n, int ell, int k, int d,
   out->pairs = cand;
   out->count = m;
   return MSM_OK;
+}
+
+int msm_enumerate(const uint64_t* strings, int64_t n, int ell, int k, int d,
+                  int Q, int flags, const msm_allocator* alloc,
+                  msm_pairs* out, msm_stats* stats, void* stream) {
+  return enumerate_impl(strings, n, nullptr, 1, ell, k, d, Q, flags, alloc, out, stats,
+                        (cudaStream_t)stream);
+}
+
+int msm_enumerate_sets(const uint64_t* strings, const int64_t* set_offsets, int nsets,
+                       int ell, int k, int d, int Q, int flags,
+                       const msm_allocator* alloc, msm_pairs* out, msm_stats* stats,
+                       void* stream) {
+  int64_t n = 0;
+  int rc = check_sets(set_offsets, nsets, &n);
+  if (rc) return rc;
+  return enumerate_impl(strings, n, set_offsets, nsets, ell, k, d, Q, flags, alloc, out, stats,
+                        (cudaStream_t)stream);
 }
 
 int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
@@ -661,11 +820,28 @@ int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
   return MSM_OK;
 }
 
-int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
-                  float eps, double miss_ratio, const msm_params* params,
-                  const msm_allocator* alloc, msm_pairs* out,
-                  msm_stats* stats, void* stream) {
-  cudaStream_t s = (cudaStream_t)stream;
+// A plan run of the count-only pipeline: the Scratch (recording or
+// replaying) and the device words the plan reads once the work is done.
+struct PlanCtx {
+  Scratch* sc = nullptr;
+  unsigned* norm_flags = nullptr;       // bit 0 zero row, bit 1 non-finite
+  unsigned* proj_status = nullptr;      // bit 0 wait timeout, bit 1 queue overflow
+  unsigned long long* ctr = nullptr;    // [0] kept, [1] eps decisions in double,
+                                        // [2] signs decided in double
+  unsigned long long* counters = nullptr;  // [0] candidates, [1] in-group pairs
+  unsigned long long* set_kept = nullptr;  // [S]
+  int Q = 0, masks = 0;
+};
+
+// The whole method over one pool (S = 1, off = NULL) or over S point sets
+// (host offsets off[0..S]); per-set result sizes into host set_counts.
+// With pc (count-only output, device X): no host round trip at all; the
+// results stay on the device at the addresses pc receives.
+static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, int dim,
+                          int dtype, int metric, float eps, double miss_ratio,
+                          const msm_params* params, const msm_allocator* alloc,
+                          msm_pairs* out, int64_t* set_counts, msm_stats* stats,
+                          cudaStream_t s, PlanCtx* pc = nullptr) {
   if (!X || !params || !out || dim < 1 || dim > kMaxDim || !(eps >= 0.f) ||
       (metric != MSM_COSINE && metric != MSM_EUCLIDEAN) ||
       (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16) ||
@@ -685,9 +861,22 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
   out->dist = nullptr;
   out->count = 0;
   if (stats) memset(stats, 0, sizeof(*stats));
-  Scratch sc(alloc, s);
+  Scratch local(alloc, s);
+  Scratch& sc = pc ? *pc->sc : local;
   PhaseTimer tm(stats != nullptr, s);
   KtScope kts(stats != nullptr);
+  if (pc && (params->out_mode != MSM_OUT_COUNT || params->Y || !is_device_ptr(X)))
+    return set_error("a plan runs count-only on device input without features"), MSM_E_INVAL;
+
+  SetTable sets;
+  rc = make_set_table(sc, off, S, n, &sets);
+  if (rc) return rc;
+  unsigned long long* set_kept = nullptr;
+  if ((set_counts || pc) && S > 1) {
+    set_kept = (unsigned long long*)sc.get(8 * (size_t)S);
+    if (!set_kept) return MSM_E_NOMEM;
+    MSM_CUDA(cudaMemsetAsync(set_kept, 0, 8 * (size_t)S, s));
+  }
 
   // Input in device memory.
   const void* Xd = X;
@@ -700,7 +889,8 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
   }
   double* n64;
   float* n32;
-  rc = norms_and_check(sc, Xd, dtype, n, dim, metric, &n64, &n32);
+  rc = norms_and_check(sc, Xd, dtype, n, dim, metric, &n64, &n32,
+                       pc ? &pc->norm_flags : nullptr);
   if (rc) return rc;
   // Projection input: X itself, or the learned features Y.
   const void* P = Xd;
@@ -734,24 +924,35 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
   MSM_CUDA(cudaMemsetAsync(ctr, 0, 256, s));
   tm.mark(1);
   rc = run_projection(sc, P, pdtype, n, pdim, R, pnorm, Q, ell, params->flags,
-                      strings, ctr + 2);
+                      strings, ctr + 2, pc ? &pc->proj_status : nullptr);
   if (rc) return rc;
 
   uint64_t* cand = nullptr;
   int64_t m = 0;
   const int mode = params->out_mode;
-  // Count only: each mask batch's candidates are rechecked as they come and
-  // dropped, so the candidate list never exceeds one batch.
-  CandSink sink;
-  if (mode == MSM_OUT_COUNT)
-    sink = [&](const uint64_t* c, int64_t cnt) -> int {
-      tm.mark(5);
-      return launch_recheck(Xd, dtype, n, dim, metric, eps, n32, c, nullptr, cnt, nullptr,
-                            nullptr, ctr, ctr + 1, s);
-    };
-  rc = run_msm(sc, strings, n, ell, k, d, Q, params->group_bits,
-               params->cand_capacity, &cand, &m, stats, tm, sink);
+  // Count only: every candidate is rechecked inside the pair check as soon
+  // as it passes, so no candidate list is stored at all.
+  FuseCfg fz;
+  if (mode == MSM_OUT_COUNT) {
+    fz.X = Xd;
+    fz.dtype = dtype;
+    fz.dim = dim;
+    fz.metric = metric;
+    fz.eps = eps;
+    fz.nrm = n32;
+    fz.kept = ctr;
+    fz.set_kept = set_kept;
+  }
+  rc = run_msm(sc, strings, n, ell, k, d, Q, tuning_of(params),
+               params->cand_capacity, &cand, &m, stats, tm, sets, fz,
+               pc ? &pc->counters : nullptr);
   if (rc) return rc;
+  if (pc) {  // results stay on the device for the plan
+    pc->ctr = ctr;
+    pc->set_kept = set_kept;
+    pc->Q = Q;
+    return MSM_OK;
+  }
   sc.put(strings);
 
   // A8: recheck into the output buffers.
@@ -781,6 +982,15 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
     rc = sort_pairs64(pairs, (uint32_t*)dist, kept, 32 + bits_for(n - 1), ws, s);
     if (rc) return rc;
   }
+  if (set_kept && pairs) {
+    rc = launch_set_counts(pairs, kept, sets.off, S, set_kept, s);
+    if (rc) return rc;
+  }
+  if (set_counts && S > 1) {
+    MSM_CUDA(cudaMemcpyAsync(set_counts, set_kept, 8 * (size_t)S, cudaMemcpyDeviceToHost, s));
+  } else if (set_counts) {
+    set_counts[0] = kept;
+  }
   tm.mark(-1);
   MSM_CUDA(cudaStreamSynchronize(s));
   if (stats) {
@@ -796,6 +1006,26 @@ int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
   out->dist = dist;
   out->count = kept;
   return MSM_OK;
+}
+
+int msm_eps_graph(const void* X, int64_t n, int dim, int dtype, int metric,
+                  float eps, double miss_ratio, const msm_params* params,
+                  const msm_allocator* alloc, msm_pairs* out,
+                  msm_stats* stats, void* stream) {
+  return eps_graph_impl(X, n, nullptr, 1, dim, dtype, metric, eps, miss_ratio, params, alloc,
+                        out, nullptr, stats, (cudaStream_t)stream);
+}
+
+int msm_eps_graph_sets(const void* X, const int64_t* set_offsets, int nsets, int dim,
+                       int dtype, int metric, float eps, double miss_ratio,
+                       const msm_params* params, const msm_allocator* alloc,
+                       msm_pairs* out, int64_t* set_counts, msm_stats* stats,
+                       void* stream) {
+  int64_t n = 0;
+  int rc = check_sets(set_offsets, nsets, &n);
+  if (rc) return rc;
+  return eps_graph_impl(X, n, set_offsets, nsets, dim, dtype, metric, eps, miss_ratio, params,
+                        alloc, out, set_counts, stats, (cudaStream_t)stream);
 }
 
 int msm_mlp_forward(const void* X, int64_t n, int dim, int dtype, const void* W1,
@@ -847,6 +1077,334 @@ int msm_mlp_adam(float* params, const float* grads, float* m, float* v, int64_t 
     return set_error("invalid msm_mlp_adam arguments"), MSM_E_INVAL;
   return mlp_adam(params, grads, m, v, count, step, lr, beta1, beta2, eps, W1_bf16, W2_bf16,
                   hidden, dim, dim_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ======================================================================
+// Reusable count-only plans (batched form).  The first run executes the
+// sync-free pipeline eagerly and logs every buffer it allocates; the second
+// captures the same pipeline, replaying those buffers, into a CUDA graph;
+// later runs launch the graph.  Every check that needs a device word (zero
+// rows, non-finite input, projection queue, wait timeouts) is read after
+// the work completes.
+struct msm_plan {
+  std::vector<int64_t> off;
+  int S = 1;
+  int64_t n = 0;
+  int dim = 0, dtype = 0, metric = 0;
+  float eps = 0.f;
+  double miss_ratio = 0.0;
+  msm_params params;
+  msm_allocator alloc;
+  bool has_alloc = false;
+  int device = 0;
+  cudaStream_t ps = nullptr;      // the plan's stream (capture needs a non-legacy one)
+  cudaEvent_t ev = nullptr, t0 = nullptr, t1 = nullptr;
+  void* input = nullptr;          // device copy of X the graph reads
+  ScratchLog log;
+  PlanCtx ctx;                    // device addresses of the recorded run
+  bool recorded = false;
+  cudaGraphExec_t exec = nullptr;
+  const msm_allocator* A() const { return has_alloc ? &alloc : nullptr; }
+};
+
+namespace msm {
+
+static void plan_reset(msm_plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  p->exec = nullptr;
+  for (int i = 0; i < p->log.count; ++i) raw_free(p->A(), p->log.ptr[i], p->ps);
+  p->log.count = p->log.next = 0;
+  p->recorded = false;
+  p->ctx = PlanCtx();
+}
+
+static int64_t choose(int k, int d) {
+  int64_t c = 1;
+  for (int i = 0; i < d; ++i) c = c * (k - i) / (i + 1);
+  return c;
+}
+
+}  // namespace msm
+
+extern "C" {
+
+int msm_plan_create(const int64_t* set_offsets, int nsets, int dim, int dtype, int metric,
+                    float eps, double miss_ratio, const msm_params* params,
+                    const msm_allocator* alloc, msm_plan** plan) {
+  if (!plan || !params) return set_error("invalid msm_plan_create arguments"), MSM_E_INVAL;
+  *plan = nullptr;
+  int64_t n = 0;
+  int rc = check_sets(set_offsets, nsets, &n);
+  if (rc) return rc;
+  if (dim < 1 || dim > kMaxDim || !(eps >= 0.f) || params->Y ||
+      (metric != MSM_COSINE && metric != MSM_EUCLIDEAN) ||
+      (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16))
+    return set_error("invalid msm_plan_create arguments"), MSM_E_INVAL;
+  rc = check_geometry(n, params->ell, params->k, params->d);
+  if (rc) return rc;
+  msm_plan* p = new msm_plan();
+  p->off.assign(set_offsets, set_offsets + nsets + 1);
+  p->S = nsets;
+  p->n = n;
+  p->dim = dim;
+  p->dtype = dtype;
+  p->metric = metric;
+  p->eps = eps;
+  p->miss_ratio = miss_ratio;
+  p->params = *params;
+  p->params.out_mode = MSM_OUT_COUNT;
+  if (alloc) {
+    p->alloc = *alloc;
+    p->has_alloc = true;
+  }
+  cudaGetDevice(&p->device);
+  if (cudaStreamCreateWithFlags(&p->ps, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&p->t0) != cudaSuccess || cudaEventCreate(&p->t1) != cudaSuccess) {
+    cudaGetLastError();
+    msm_plan_destroy(p, nullptr);
+    return set_error("plan stream or event creation failed"), MSM_E_CUDA;
+  }
+  p->input = raw_alloc(p->A(), dtype_size(dtype) * (size_t)n * dim, p->ps);
+  if (!p->input) {
+    msm_plan_destroy(p, nullptr);
+    return MSM_E_NOMEM;
+  }
+  *plan = p;
+  return MSM_OK;
+}
+
+void* msm_plan_input(msm_plan* plan) { return plan ? plan->input : nullptr; }
+
+int msm_plan_run(msm_plan* p, const void* X, int64_t* count, int64_t* set_counts,
+                 msm_stats* stats, void* stream) {
+  if (!p || !count) return set_error("invalid msm_plan_run arguments"), MSM_E_INVAL;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device) return set_error("msm_plan_run on another device"), MSM_E_INVAL;
+  cudaStream_t us = (cudaStream_t)stream;
+  const size_t xbytes = dtype_size(p->dtype) * (size_t)p->n * p->dim;
+  // order after the caller's stream (X may be written there)
+  MSM_CUDA(cudaEventRecord(p->ev, us));
+  MSM_CUDA(cudaStreamWaitEvent(p->ps, p->ev, 0));
+  if (X && X != p->input)
+    MSM_CUDA(cudaMemcpyAsync(p->input, X, xbytes, cudaMemcpyDefault, p->ps));
+  MSM_CUDA(cudaEventRecord(p->t0, p->ps));
+  msm_pairs out;
+  if (!p->recorded) {
+    Scratch sc(p->A(), p->ps, &p->log, false);
+    p->ctx = PlanCtx();
+    p->ctx.sc = &sc;
+    int rc = eps_graph_impl(p->input, p->n, p->off.data(), p->S, p->dim, p->dtype, p->metric,
+                            p->eps, p->miss_ratio, &p->params, p->A(), &out, nullptr, nullptr,
+                            p->ps, &p->ctx);
+    p->ctx.sc = nullptr;
+    if (rc) {
+      cudaStreamSynchronize(p->ps);
+      plan_reset(p);
+      return rc;
+    }
+    p->recorded = true;
+  } else if (!p->exec) {
+    p->log.next = 0;
+    Scratch sc(p->A(), p->ps, &p->log, true);
+    PlanCtx c;
+    c.sc = &sc;
+    MSM_CUDA(cudaStreamBeginCapture(p->ps, cudaStreamCaptureModeThreadLocal));
+    int rc = eps_graph_impl(p->input, p->n, p->off.data(), p->S, p->dim, p->dtype, p->metric,
+                            p->eps, p->miss_ratio, &p->params, p->A(), &out, nullptr, nullptr,
+                            p->ps, &c);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(p->ps, &g);
+    if (rc || ce != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return rc ? rc : cuda_fail(ce, "cudaStreamEndCapture");
+    }
+    if (c.ctr != p->ctx.ctr || c.counters != p->ctx.counters || c.set_kept != p->ctx.set_kept) {
+      cudaGraphDestroy(g);
+      return set_error("plan capture used other buffers than the recorded run"), MSM_E_INVAL;
+    }
+    ce = cudaGraphInstantiate(&p->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      p->exec = nullptr;
+      return cuda_fail(ce, "cudaGraphInstantiate");
+    }
+    MSM_CUDA(cudaGraphLaunch(p->exec, p->ps));
+  } else {
+    MSM_CUDA(cudaGraphLaunch(p->exec, p->ps));
+  }
+  MSM_CUDA(cudaEventRecord(p->t1, p->ps));
+  // read the results and the deferred checks
+  unsigned long long ctr[3] = {0, 0, 0}, cnt[2] = {0, 0};
+  unsigned nf = 0, ps_st = 0;
+  std::vector<unsigned long long> sk(p->S > 1 ? (size_t)p->S : 0);
+  MSM_CUDA(cudaMemcpyAsync(ctr, p->ctx.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, p->ps));
+  MSM_CUDA(cudaMemcpyAsync(cnt, p->ctx.counters, sizeof(cnt), cudaMemcpyDeviceToHost, p->ps));
+  MSM_CUDA(cudaMemcpyAsync(&nf, p->ctx.norm_flags, sizeof(nf), cudaMemcpyDeviceToHost, p->ps));
+  if (p->ctx.proj_status)
+    MSM_CUDA(cudaMemcpyAsync(&ps_st, p->ctx.proj_status, sizeof(ps_st), cudaMemcpyDeviceToHost,
+                             p->ps));
+  if (!sk.empty() && p->ctx.set_kept)
+    MSM_CUDA(cudaMemcpyAsync(sk.data(), p->ctx.set_kept, 8 * sk.size(), cudaMemcpyDeviceToHost,
+                             p->ps));
+  MSM_CUDA(cudaStreamSynchronize(p->ps));
+  if (nf & 2u) return set_error("input contains NaN or Inf"), MSM_E_NONFINITE;
+  if ((nf & 1u) && p->metric == MSM_COSINE)
+    return set_error("cosine distance is undefined for an all-zero row"), MSM_E_ZERO_NORM;
+  if (ps_st & 1u) return set_error("tensor-core projection: a bounded wait timed out"), MSM_E_TIMEOUT;
+  if (ps_st & 2u) {
+    // the tensor-core projection's queue of undecided signs overflowed: the
+    // result is incomplete.  Answer this call on the CUDA-core projection
+    // and rebuild the plan on it.
+    plan_reset(p);
+    p->params.flags |= MSM_FLAG_SIMT_PROJECTION;
+    return msm_plan_run(p, nullptr, count, set_counts, stats, stream);
+  }
+  *count = (int64_t)ctr[0];
+  if (set_counts) {
+    if (p->S > 1)
+      for (int j = 0; j < p->S; ++j) set_counts[j] = (int64_t)sk[(size_t)j];
+    else
+      set_counts[0] = (int64_t)ctr[0];
+  }
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->Q = p->ctx.Q;
+    stats->masks = (int64_t)p->ctx.Q * choose(p->params.k, p->params.d);
+    stats->cand = (int64_t)cnt[0];
+    stats->checks = (int64_t)cnt[1];
+    stats->type1 = (int64_t)cnt[0] - (int64_t)ctr[0];
+    stats->dist_recompute = (int64_t)ctr[1];
+    stats->proj_recompute = (int64_t)ctr[2];
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->t0, p->t1) == cudaSuccess) stats->ms[7] = ms;
+  }
+  return MSM_OK;
+}
+
+int msm_plan_is_graph(const msm_plan* plan) { return plan && plan->exec ? 1 : 0; }
+
+void msm_plan_destroy(msm_plan* p, void* stream) {
+  (void)stream;
+  if (!p) return;
+  if (p->ps) cudaStreamSynchronize(p->ps);
+  plan_reset(p);
+  if (p->input) raw_free(p->A(), p->input, p->ps);
+  if (p->ps) {
+    cudaStreamSynchronize(p->ps);
+    cudaStreamDestroy(p->ps);
+  }
+  if (p->ev) cudaEventDestroy(p->ev);
+  if (p->t0) cudaEventDestroy(p->t0);
+  if (p->t1) cudaEventDestroy(p->t1);
+  delete p;
+}
+
+// Autotuner of the count-only launch knobs: times each candidate setting
+// with CUDA events on the caller's input (at most 2 replicates per trial;
+// every replicate runs the same kernels) and keeps the fastest.  Results
+// are cached per device and shape in a text file of "key<TAB>min_blocks
+// ctas_per_sm masks_per_batch" lines.
+int msm_autotune(const void* X, const int64_t* set_offsets, int nsets, int dim, int dtype,
+                 int metric, float eps, msm_params* params, const char* cache_path,
+                 const msm_allocator* alloc, void* stream) {
+  if (!X || !params) return set_error("invalid msm_autotune arguments"), MSM_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t n = 0;
+  int rc = check_sets(set_offsets, nsets, &n);
+  if (rc) return rc;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  MSM_CUDA(cudaGetDeviceProperties(&prop, dev));
+  char key[512];
+  snprintf(key, sizeof(key), "%s|sm%d|n%lld|S%d|dim%d|dt%d|m%d|eps%.9g|l%d|k%d|d%d|Q%d|f%d",
+           prop.name, prop.multiProcessorCount, (long long)n, nsets, dim, dtype, metric,
+           (double)eps, params->ell, params->k, params->d, params->Q, params->flags);
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[768];
+      bool hit = false;
+      while (fgets(line, sizeof(line), f)) {
+        char* tab = strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        int mb = 0, cps = 0, mpb = 0;
+        if (strcmp(line, key) == 0 && sscanf(tab + 1, "%d %d %d", &mb, &cps, &mpb) == 3) {
+          params->check_min_blocks = mb;
+          params->check_ctas_per_sm = cps;
+          params->masks_per_batch = mpb;
+          hit = true;
+        }
+      }
+      fclose(f);
+      if (hit) return MSM_OK;
+    }
+  }
+  struct Cand {
+    int mb, cps, mpb;
+  };
+  std::vector<Cand> cands = {{4, 6, 0}, {2, 6, 0}, {5, 6, 0}, {5, 8, 0}};
+  msm_params tp = *params;
+  tp.out_mode = MSM_OUT_COUNT;
+  tp.Q = params->Q > 0 ? (params->Q < 2 ? params->Q : 2) : 1;
+  cudaEvent_t e0, e1;
+  MSM_CUDA(cudaEventCreate(&e0));
+  MSM_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  Cand bc = cands[0];
+  auto trial = [&](const Cand& c, float* ms) -> int {
+    tp.check_min_blocks = c.mb;
+    tp.check_ctas_per_sm = c.cps;
+    tp.masks_per_batch = c.mpb;
+    msm_pairs out;
+    cudaEventRecord(e0, s);
+    int r = eps_graph_impl(X, n, set_offsets, nsets, dim, dtype, metric, eps, 1e-6, &tp, alloc,
+                           &out, nullptr, nullptr, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    *ms = 0.f;
+    cudaEventElapsedTime(ms, e0, e1);
+    return r;
+  };
+  float ms = 0.f;
+  rc = trial(cands[0], &ms);  // warm-up (first-touch allocations)
+  for (size_t i = 0; !rc && i < cands.size(); ++i) {
+    rc = trial(cands[i], &ms);
+    if (!rc && ms < best) {
+      best = ms;
+      bc = cands[i];
+    }
+  }
+  // then the grouping batch size, with the best pair-check setting
+  const int M = (int)choose(params->k, params->d);
+  for (int div : {2, 4}) {
+    const int mpb = (M + div - 1) / div;
+    if (rc || mpb < 1 || mpb >= M) continue;
+    Cand c{bc.mb, bc.cps, mpb};
+    rc = trial(c, &ms);
+    if (!rc && ms < best) {
+      best = ms;
+      bc = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  params->check_min_blocks = bc.mb;
+  params->check_ctas_per_sm = bc.cps;
+  params->masks_per_batch = bc.mpb;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "a")) {
+      fprintf(f, "%s\t%d %d %d\n", key, bc.mb, bc.cps, bc.mpb);
+      fclose(f);
+    }
+  }
+  return MSM_OK;
 }
 
 void msm_free_pairs(msm_pairs* p, const msm_allocator* alloc, void* stream) {

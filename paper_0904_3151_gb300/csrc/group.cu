@@ -109,9 +109,42 @@ struct SortArgs {
   int64_t n;       // items per segment
   int tiles;       // tiles per segment
   int shift;       // digit shift of this pass
-  uint32_t* counts;         // [S][256][tiles]
+  uint32_t* counts;         // [S][256][tiles] (per set: [256][set's tiles])
   const uint32_t* offsets;  // exclusive scan of counts
+  // point sets (NULL tile_set: the segment is one set)
+  const int* tile_set;
+  const int* set_tile0;
+  const int64_t* set_off;
 };
+
+// Items of radix tile `tile` of a segment: [base, base + cnt) of the
+// segment, with the tile's counter index for digit 0 and the counter stride
+// between digits.  Within a segment the counters are laid out set by set,
+// digit-major inside a set, so one exclusive scan over all counters gives
+// every (segment, set, digit, tile) its output position and every set of a
+// segment stays in place.
+struct TileSpan {
+  int64_t base, cnt, cidx, cstride;
+};
+
+__device__ __forceinline__ TileSpan tile_span(const SortArgs& a, int seg, int tile,
+                                              int tile_items) {
+  int64_t lo = 0, hi = a.n, tile0 = 0, tiles_s = a.tiles;
+  if (a.tile_set) {
+    const int ss = a.tile_set[tile];
+    lo = a.set_off[ss];
+    hi = a.set_off[ss + 1];
+    tile0 = a.set_tile0[ss];
+    tiles_s = a.set_tile0[ss + 1] - tile0;
+  }
+  const int64_t t = tile - tile0;
+  TileSpan sp;
+  sp.base = lo + t * tile_items;
+  sp.cnt = min((int64_t)tile_items, hi - sp.base);
+  sp.cidx = (int64_t)seg * kRadix * a.tiles + kRadix * tile0 + t;
+  sp.cstride = tiles_s;
+  return sp;
+}
 
 template <typename KeyT, bool FROM_STR>
 __device__ __forceinline__ KeyT load_key(const SortArgs& a, const KeptList& kl,
@@ -134,8 +167,8 @@ hist_kernel(SortArgs a) {
   for (int t = tid; t < (kThreads / 32) * kRadix; t += kThreads) (&h[0][0])[t] = 0;
   if constexpr (FROM_STR) setup_kept(kl, a.masks[seg], a.layout, a.group_bits);
   __syncthreads();
-  const int64_t base = (int64_t)tile * TILE;
-  const int64_t cnt = min((int64_t)TILE, a.n - base);
+  const TileSpan sp = tile_span(a, seg, tile, TILE);
+  const int64_t base = sp.base, cnt = sp.cnt;
 #pragma unroll 4
   for (int j = 0; j < IPT; ++j) {
     int e = j * kThreads + tid;
@@ -150,7 +183,7 @@ hist_kernel(SortArgs a) {
   uint32_t sum = 0;
 #pragma unroll
   for (int w = 0; w < kThreads / 32; ++w) sum += h[w][tid];
-  a.counts[((int64_t)seg * kRadix + tid) * a.tiles + tile] = sum;
+  a.counts[sp.cidx + (int64_t)tid * sp.cstride] = sum;
 }
 
 // Exclusive scan of one value per thread across the CTA (256 threads).
@@ -197,8 +230,8 @@ scatter_kernel(SortArgs a) {
   for (int t = tid; t < (kThreads / 32) * kRadix; t += kThreads) (&wh[0][0])[t] = 0;
   if constexpr (FROM_STR) setup_kept(kl, a.masks[seg], a.layout, a.group_bits);
   __syncthreads();
-  const int64_t base = (int64_t)tile * TILE;
-  const int64_t cnt = min((int64_t)TILE, a.n - base);
+  const TileSpan sp = tile_span(a, seg, tile, TILE);
+  const int64_t base = sp.base, cnt = sp.cnt;
   const unsigned lt_mask = (1u << lane) - 1u;
 
   KeyT key[IPT];
@@ -243,7 +276,7 @@ scatter_kernel(SortArgs a) {
   }
   uint32_t start = block_exclusive_scan(run, tmp);
   dstart[tid] = start;
-  gofs[tid] = a.offsets[((int64_t)seg * kRadix + tid) * a.tiles + tile];
+  gofs[tid] = a.offsets[sp.cidx + (int64_t)tid * sp.cstride];
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
@@ -427,9 +460,11 @@ constexpr int kIpt32 = 16;
 constexpr int kTile32 = kThreads * kIpt32;
 }
 
-size_t group_scratch_bytes(int64_t n, int S) {
+int group_tile_items() { return kTile32; }
+
+size_t group_scratch_bytes(int64_t n, int S, int nsets) {
   int64_t items = n * S;
-  int64_t tiles = (n + kTile32 - 1) / kTile32;
+  int64_t tiles = (n + kTile32 - 1) / kTile32 + (nsets > 1 ? nsets : 0);
   int64_t counts = (int64_t)S * kRadix * tiles;
   return 4 * align256(sizeof(uint32_t) * (size_t)items) +
          2 * align256(sizeof(uint32_t) * (size_t)counts) +
@@ -439,7 +474,7 @@ size_t group_scratch_bytes(int64_t n, int S) {
 int run_grouping(const GroupBatch& b, void* ws, uint32_t** keys_out,
                  uint32_t** vals_out, cudaStream_t s) {
   const int64_t items = b.n * b.S;
-  const int tiles = (int)((b.n + kTile32 - 1) / kTile32);
+  const int tiles = b.sets.tile_set ? b.sets.T : (int)((b.n + kTile32 - 1) / kTile32);
   const int64_t ncounts = (int64_t)b.S * kRadix * tiles;
   if (items >= (1ll << 32)) return set_error("grouping batch too large"), MSM_E_INVAL;
   char* p = reinterpret_cast<char*>(ws);
@@ -461,6 +496,10 @@ int run_grouping(const GroupBatch& b, void* ws, uint32_t** keys_out,
   a.tiles = tiles;
   a.counts = counts;
   a.offsets = offsets;
+  a.tile_set = b.sets.tile_set;
+  a.set_tile0 = b.sets.set_tile0;
+  a.set_off = b.sets.off;
+  if (tiles == 0) return set_error("grouping: no radix tiles"), MSM_E_INVAL;
   dim3 grid(tiles, b.S);
   uint32_t *ki = nullptr, *vi = nullptr, *ko = kA, *vo = vA;
   for (int pass = 0; pass < b.passes; ++pass) {

@@ -75,23 +75,42 @@ struct KtScope {  // installs a per-call timer for this thread
 };
 
 // ------------------------------------------------------------ scratch
+// Buffers of a reusable execution plan, in the order they were requested.
+struct ScratchLog {
+  void* ptr[128];
+  size_t bytes[128];
+  int count = 0;
+  int next = 0;   // replay position
+};
+
 // Device memory for one call: every buffer comes from the caller's
 // allocator (or cudaMallocAsync) and is released, stream-ordered, when the
 // Scratch goes out of scope, except buffers handed over with release().
+// Plan modes (a ScratchLog): recording allocates and logs every buffer and
+// frees nothing (the plan owns them); replaying hands the logged buffers out
+// again in the same order, so a captured CUDA graph sees exactly the
+// buffers of the recorded run.  Both modes mark the call as sync-free:
+// checks that would read a device word back are deferred to the plan.
 class Scratch {
  public:
   Scratch(const msm_allocator* a, cudaStream_t s) : a_(a), s_(s) {}
+  Scratch(const msm_allocator* a, cudaStream_t s, ScratchLog* log, bool replay)
+      : a_(a), s_(s), log_(log), replay_(replay) {}
   ~Scratch();
   void* get(size_t bytes);          // NULL on failure (error message set)
   void put(void* p);                // free now (stream-ordered)
   void release(void* p);            // hand ownership to the caller
   cudaStream_t stream() const { return s_; }
   const msm_allocator* allocator() const { return a_; }
+  bool sync_free() const { return log_ != nullptr; }
+  bool replaying() const { return replay_; }
  private:
   const msm_allocator* a_;
   cudaStream_t s_;
   void* live_[64];
   int nlive_ = 0;
+  ScratchLog* log_ = nullptr;
+  bool replay_ = false;
 };
 
 void* raw_alloc(const msm_allocator* a, size_t bytes, cudaStream_t s);
@@ -120,12 +139,29 @@ int launch_project(const void* X, int dtype, int64_t n, int dim,
 bool tc_project_supported(int dtype, int dim, uintptr_t xaddr);
 size_t tc_project_scratch_bytes(int64_t n, int dim, int Q, int ell, int dtype);
 // *fell_back = true when the queue overflowed (the caller must then run the
-// SIMT projection, which overwrites every string).
+// SIMT projection, which overwrites every string).  fell_back == NULL: no
+// host round trip; an overflow is reported in *status bit 1 instead.
 int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
                       const float* R, const float* xnorm, int Q, int ell,
                       uint64_t* strings, unsigned long long* recompute,
                       void* ws, unsigned* status, bool* fell_back,
                       cudaStream_t s);
+
+// Point sets of a batched call: set s holds the points [off[s], off[s+1])
+// of the pool, and a group (run of equal grouping keys) never spans two
+// sets.  A single pool is one set with all pointers NULL.
+struct SetTable {
+  int S = 1;                            // sets
+  const int64_t* off = nullptr;         // device [S+1]
+  const int* tile_set = nullptr;        // device [T]: set of each radix tile
+  const int* set_tile0 = nullptr;       // device [S+1]: first radix tile of each set
+  const uint32_t* start_bits = nullptr; // device bitmap over points: bit p set
+                                        // iff some set other than the first
+                                        // starts at point p
+  int T = 0;                            // radix tiles per grouping segment
+};
+// Items per radix tile of the grouping sort (tiles never straddle sets).
+int group_tile_items();
 
 // group.cu: grouping of every (mask, string) of a batch of masks.
 struct GroupBatch {
@@ -137,8 +173,9 @@ struct GroupBatch {
   int group_bits;           // key width (8..32)
   int passes;               // ceil(group_bits / 8)
   const BlockLayout* layout;  // device copy
+  SetTable sets;            // point sets (one set: defaults)
 };
-size_t group_scratch_bytes(int64_t n, int S);
+size_t group_scratch_bytes(int64_t n, int S, int nsets = 1);
 // Sorts (key, index) of all S*n items by key within each mask segment;
 // on return keys/vals hold the sorted order (pointers into `ws`).
 int run_grouping(const GroupBatch& b, void* ws, uint32_t** keys_out,
@@ -176,6 +213,22 @@ struct PairBatch {
   const uint32_t* fields;    // optional field layout [Q][n][FP] (or NULL)
   int FP;                    // stored words per string (even)
   int FU;                    // words holding fields, ceil(k / 2)
+  const uint32_t* start_bits = nullptr;  // set starts (SetTable::start_bits)
+  // Fused recheck (count-only output): when X is set, every pair that passes
+  // the tests is rechecked against eps at once and counted; nothing is
+  // appended to the candidate list.
+  const void* X = nullptr;
+  int dtype = 0, dim = 0, metric = 0;
+  float eps = 0.f;
+  const float* nrm = nullptr;            // float row norms (cosine)
+  unsigned long long* kept = nullptr;    // [0] pairs within eps,
+                                         // [1] double-precision decisions
+  unsigned long long* set_kept = nullptr;  // per-set pairs within eps (or NULL)
+  const int64_t* set_off = nullptr;      // device [nsets + 1]
+  int nsets = 1;
+  // launch tuning of the pair check (0 = defaults)
+  int ctas_per_sm = 0;
+  int min_blocks = 0;                    // fused variant: 2, 4 or 5
 };
 size_t pairs_scratch_bytes(int64_t items);
 // Field layout: every block in its own 16-bit field, FP (even) words per
@@ -191,6 +244,10 @@ int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
 // this (replicate, mask) to cand (capacity cap) at *count_dev.
 int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
                  unsigned long long* count_dev, cudaStream_t s);
+
+// Per-set pair counts of a finished pair list (counts: device [S], added to).
+int launch_set_counts(const uint64_t* pairs, int64_t m, const int64_t* off, int S,
+                      unsigned long long* counts, cudaStream_t s);
 
 // mlp.cu: learned projection network
 int mlp_forward(const void* X, int dtype, int64_t n, int dim, const void* W1,

@@ -14,7 +14,7 @@
 // warp (its C(b,2) pairs spread over the lanes); a larger run is split into
 // 32 x 32 tiles of its upper triangle, one tile per work item.  Warps take
 // contiguous ranges of work items.
-#include "msm_internal.cuh"
+#include "distance.cuh"
 
 namespace msm {
 namespace {
@@ -91,21 +91,32 @@ __global__ void chunk_index_kernel(const uint64_t* work_prefix,
   }
 }
 
+__device__ __forceinline__ bool bit_at(const uint32_t* bits, int64_t i) {
+  return (bits[i >> 5] >> (i & 31)) & 1u;
+}
+
 // Run boundary flags of flat position p whose offset in its segment (of
 // length n) is `local`; runs are equal K-block parts of the key (the key
-// shifted right by the segment's sub-key width sw).
+// shifted right by the segment's sub-key width sw) inside one point set
+// (sb: set starts, or NULL for a single set).
 __device__ __forceinline__ void run_flags(const uint32_t* keys, int64_t n,
                                           int64_t p, int64_t local, int sw,
-                                          bool& start, bool& end) {
+                                          const uint32_t* sb, bool& start,
+                                          bool& end) {
   uint32_t k = keys[p] >> sw;
   bool head = (local == 0) || (keys[p - 1] >> sw) != k;
   bool tail = (local == n - 1) || (keys[p + 1] >> sw) != k;
+  if (sb) {
+    head = head || bit_at(sb, local);
+    tail = tail || (local + 1 < n && bit_at(sb, local + 1));
+  }
   start = head && !tail;
   end = tail && !head;
 }
 
 __global__ void run_count_kernel(const uint32_t* keys, int64_t items, int64_t n,
-                                 const MaskDesc* masks, uint32_t* cnt_start,
+                                 const MaskDesc* masks, const uint32_t* sb,
+                                 uint32_t* cnt_start,
                                  uint32_t* cnt_end) {
   int64_t p0 = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * 16;
   uint32_t cs = 0, ce = 0;
@@ -121,7 +132,7 @@ __global__ void run_count_kernel(const uint32_t* keys, int64_t items, int64_t n,
     int64_t p = p0 + j;
     if (p < items) {
       bool s, e;
-      run_flags(keys, n, p, local, sw, s, e);
+      run_flags(keys, n, p, local, sw, sb, s, e);
       cs += s;
       ce += e;
     }
@@ -167,7 +178,7 @@ __device__ __forceinline__ uint32_t block_excl(uint32_t v, uint32_t* tmp,
 }
 
 __global__ void run_write_kernel(const uint32_t* keys, int64_t items, int64_t n,
-                                 const MaskDesc* masks,
+                                 const MaskDesc* masks, const uint32_t* sb,
                                  const uint32_t* off_start,
                                  const uint32_t* off_end, uint32_t* starts,
                                  uint32_t* ends, int64_t nchunks,
@@ -187,7 +198,7 @@ __global__ void run_write_kernel(const uint32_t* keys, int64_t items, int64_t n,
     int64_t p = p0 + j;
     if (p < items) {
       bool s, e;
-      run_flags(keys, n, p, local, sw, s, e);
+      run_flags(keys, n, p, local, sw, sb, s, e);
       fs |= (uint32_t)s << j;
       fe |= (uint32_t)e << j;
     }
@@ -246,7 +257,138 @@ struct CheckArgs {
   uint64_t* cand;
   int64_t cap;
   unsigned long long* count;
+  // fused recheck (count-only output), see PairBatch
+  const void* X;
+  int dtype, dim, metric;
+  float eps, relS;
+  const float* nrm;
+  unsigned long long* kept;
+  unsigned long long* set_kept;
+  const int64_t* set_off;
+  int nsets;
 };
+
+// ------------------------------------------------------- fused recheck
+// In count-only mode the pairs that pass the tests of a work item are not
+// appended to a candidate list: the warp queues them in shared memory (32 at
+// a time) and evaluates their distances right away, 4 lanes per pair and 8
+// pairs per step, with the decision rule of the stand-alone recheck.  Counts
+// stay in registers (warp-uniform) until the set of the work item changes or
+// the warp finishes.
+struct FuseAcc {
+  unsigned long long cand = 0;   // pairs that passed the tests (warp-uniform)
+  unsigned long long kept = 0;   // of those, within eps (warp-uniform)
+  unsigned long long nre = 0;    // double-precision decisions (per lane)
+  unsigned long long mark = 0;   // kept at the start of the current set
+  int set = -1;
+};
+
+// Set of point p: the largest s with off[s] <= p.
+__device__ __forceinline__ int set_of(const int64_t* off, int S, int64_t p) {
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void fuse_flush_set(const CheckArgs& a, FuseAcc& acc, int lane) {
+  if (a.set_kept && acc.set >= 0 && acc.kept > acc.mark && lane == 0)
+    atomicAdd(a.set_kept + acc.set, acc.kept - acc.mark);
+  acc.mark = acc.kept;
+}
+
+// Work item of group start st begins: switch the per-set counter if needed.
+__device__ __forceinline__ void fuse_enter(const CheckArgs& a, FuseAcc& acc, uint32_t first_point,
+                                           int lane) {
+  if (!a.set_kept) return;
+  const int s = set_of(a.set_off, a.nsets, first_point);
+  if (s != acc.set) {
+    fuse_flush_set(a, acc, lane);
+    acc.set = s;
+  }
+}
+
+__device__ __forceinline__ void fuse_finish(const CheckArgs& a, FuseAcc& acc, int lane) {
+  fuse_flush_set(a, acc, lane);
+  unsigned long long nre = acc.nre;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, o);
+  if (lane == 0) {
+    if (acc.cand) atomicAdd(a.count, acc.cand);
+    if (acc.kept) atomicAdd(a.kept, acc.kept);
+    if (nre) atomicAdd(a.kept + 1, nre);
+  }
+}
+
+// Distances of the nb <= 32 queued pairs q[0..nb).
+__device__ __forceinline__ void fuse_eval(const CheckArgs& a, const uint64_t* q, uint32_t nb,
+                                          int lane, FuseAcc& acc) {
+  const int sl = lane & 3, grp = lane >> 2;
+  for (uint32_t r = 0; r < nb; r += 8) {
+    const uint32_t slot = r + (uint32_t)grp;
+    const bool valid = slot < nb;
+    const uint64_t pr = valid ? q[slot] : 0ull;
+    const int64_t i = (int64_t)(pr >> 32), j = (int64_t)(pr & 0xffffffffu);
+    const float S = dist::group_sq_dist<4>(a.X, a.dtype, i, j, a.dim, sl);
+    bool keep = false;
+    if (valid && sl == 0) {
+      const float ni = a.metric == MSM_COSINE ? a.nrm[i] : 0.f;
+      const float nj = a.metric == MSM_COSINE ? a.nrm[j] : 0.f;
+      bool exact = false;
+      dist::decide(a.X, a.dtype, i, j, a.dim, a.metric, a.eps, S, ni, nj, a.relS, false,
+                   &keep, &exact);
+      acc.nre += exact;
+    }
+    acc.kept += (unsigned long long)__popc(__ballot_sync(0xffffffffu, keep));
+  }
+}
+
+__device__ __forceinline__ uint64_t ordered_pair(uint32_t x, uint32_t y) {
+  return x < y ? (((uint64_t)x << 32) | y) : (((uint64_t)y << 32) | x);
+}
+
+// At most one passing pair (ii, jj) per lane.
+__device__ __forceinline__ void fuse_one(const CheckArgs& a, bool pass, uint32_t ii, uint32_t jj,
+                                         int lane, uint64_t* q, FuseAcc& acc) {
+  const unsigned bal = __ballot_sync(0xffffffffu, pass);
+  if (!bal) return;
+  if (pass) q[__popc(bal & ((1u << lane) - 1u))] = ordered_pair(ii, jj);
+  __syncwarp();
+  acc.cand += (unsigned long long)__popc(bal);
+  fuse_eval(a, q, (uint32_t)__popc(bal), lane, acc);
+  __syncwarp();
+}
+
+// The pairs (ia, ib[c]) for the set bits c of each lane's mask.
+__device__ __forceinline__ void fuse_mask(const CheckArgs& a, uint32_t mask, uint32_t ia,
+                                          const uint32_t* ib, int lane, uint64_t* q,
+                                          FuseAcc& acc) {
+  const uint32_t cnt = __popc(mask);
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) return;
+  acc.cand += total;
+  const uint32_t excl = incl - cnt;
+  for (uint32_t b0 = 0; b0 < total; b0 += 32) {
+    uint32_t m = mask, pos = excl;
+    while (m) {
+      const int c = __ffs(m) - 1;
+      m &= m - 1;
+      if (pos >= b0 && pos < b0 + 32) q[pos - b0] = ordered_pair(ia, ib[c]);
+      ++pos;
+    }
+    __syncwarp();
+    fuse_eval(a, q, min(32u, total - b0), lane, acc);
+    __syncwarp();
+  }
+}
 
 // The tests of one pair, most selective first:
 //   first-mask rule, part 1: every gap block (below max K, not kept)
@@ -337,11 +479,17 @@ __device__ __forceinline__ void emit_mask(const CheckArgs& a, uint32_t mask,
   }
 }
 
-template <int W>
-__global__ void __launch_bounds__(kThreads)
+// MINB: resident CTAs per SM the register allocation must allow (0: no
+// constraint, the compiler's choice).  The fused
+// (count-only) variants hold the distance evaluation's loads in registers;
+// capping them keeps the integer tests at full occupancy, at the price of
+// spills on the rarely taken recheck path.
+template <int W, bool FUSE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 check_kernel(CheckArgs a) {
   __shared__ uint64_t sm_s[kThreads / 32][32][W];
   __shared__ uint32_t sm_i[kThreads / 32][32];
+  __shared__ uint64_t sm_q[kThreads / 32][32];  // fused recheck queue
   __shared__ uint64_t bm[kMaxBlocks][W];
   __shared__ uint64_t sm_gm[kThreads / 32][kMaxBlocks][W];  // gap block masks
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -354,6 +502,8 @@ check_kernel(CheckArgs a) {
   const uint64_t C = chunk_size(total, a.chunk_cap);
   const uint64_t nch = (total + C - 1) / C;
   const uint64_t* pool = a.strings + (size_t)a.q * a.n * W;
+  FuseAcc acc;
+  uint32_t cur_g = 0xffffffffu;
   int cur_seg = -1, ngap = 0;
   bool hashed = false;
   uint64_t keep[W];
@@ -379,6 +529,10 @@ check_kernel(CheckArgs a) {
     const uint32_t st = a.starts[g];
     const uint32_t len = a.ends[g] - st + 1;
     const int seg = (int)(st / a.n);
+    if (FUSE && g != cur_g) {
+      cur_g = g;
+      fuse_enter(a, acc, a.vals[st], lane);
+    }
     if (seg != cur_seg) {  // this grouping's first-mask test data
       const MaskDesc& md = a.masks[seg];
       cur_seg = seg;
@@ -424,6 +578,10 @@ check_kernel(CheckArgs a) {
             const uint32_t i0 = ii < jj ? ii : jj, j0 = ii < jj ? jj : ii;
             pass = replicates_ok<W>(a, i0, j0);
           }
+        }
+        if constexpr (FUSE) {
+          fuse_one(a, pass, ii, jj, lane, sm_q[warp], acc);
+          continue;
         }
         // one pair per lane: a ballot gives the positions
         const unsigned bal = __ballot_sync(0xffffffffu, pass);
@@ -474,11 +632,13 @@ check_kernel(CheckArgs a) {
           }
         }
       }
-      emit_mask(a, passm, ia, sm_i[warp], lane);
+      if constexpr (FUSE) fuse_mask(a, passm, ia, sm_i[warp], lane, sm_q[warp], acc);
+      else emit_mask(a, passm, ia, sm_i[warp], lane);
       __syncwarp();
     }
   }
   }
+  if constexpr (FUSE) fuse_finish(a, acc, lane);
 }
 
 // ------------------------------------------------- field-layout variant
@@ -584,11 +744,12 @@ __device__ __forceinline__ bool replicates_ok_fields(const CheckArgs& a,
   return true;
 }
 
-template <int FP, int FU>
-__global__ void __launch_bounds__(kThreads)
+template <int FP, int FU, bool FUSE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 check_fields_kernel(CheckArgs a, const uint32_t* fields) {
   __shared__ __align__(16) uint32_t sm_f[kThreads / 32][32][FP];
   __shared__ uint32_t sm_i[kThreads / 32][32];
+  __shared__ uint64_t sm_q[kThreads / 32][32];  // fused recheck queue
   // pair p of a group of <= 32 items, column by column: p = b(b-1)/2 + a
   __shared__ uint8_t tri_a[496], tri_b[496];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -605,6 +766,8 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
   const uint64_t C = chunk_size(total, a.chunk_cap);
   const uint64_t nch = (total + C - 1) / C;
   const uint32_t* pool = fields + (size_t)a.q * a.n * FP;
+  FuseAcc acc;
+  uint32_t cur_g = 0xffffffffu;
   int cur_seg = -1, subw = 0;
   bool hashed = false;
   uint32_t gapf[FP], keepf[FP];
@@ -623,6 +786,10 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
     const uint32_t st = a.starts[g];
     const uint32_t len = a.ends[g] - st + 1;
     const int seg = (int)(st / a.n);
+    if (FUSE && g != cur_g) {
+      cur_g = g;
+      fuse_enter(a, acc, a.vals[st], lane);
+    }
     if (seg != cur_seg) {
       const MaskDesc& md = a.masks[seg];
       cur_seg = seg;
@@ -670,6 +837,10 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
             jj = sm_i[warp][b];
             pass = replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj, ii < jj ? jj : ii);
           }
+        }
+        if constexpr (FUSE) {
+          fuse_one(a, pass, ii, jj, lane, sm_q[warp], acc);
+          continue;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, pass);
         if (bal) {
@@ -750,14 +921,45 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
             passm |= 1u << c;
         }
       }
-      emit_mask(a, passm, ia, sm_i[warp], lane);
+      if constexpr (FUSE) fuse_mask(a, passm, ia, sm_i[warp], lane, sm_q[warp], acc);
+      else emit_mask(a, passm, ia, sm_i[warp], lane);
       __syncwarp();
     }
   }
   }
+  if constexpr (FUSE) fuse_finish(a, acc, lane);
+}
+
+// Pairs of a finished list per point set: counts[set of i] += 1 for every
+// pair (i, j) (both points lie in one set).
+__global__ void set_count_kernel(const uint64_t* pairs, int64_t m, const int64_t* off, int S,
+                                 unsigned long long* counts) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < m; base += nwarps * 32) {
+    const int64_t t = base + lane;
+    const int s = t < m ? set_of(off, S, (int64_t)(pairs[t] >> 32)) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, s);
+    if (s >= 0 && lane == __ffs(peers) - 1)
+      atomicAdd(counts + s, (unsigned long long)__popc(peers));
+  }
 }
 
 }  // namespace
+
+int launch_set_counts(const uint64_t* pairs, int64_t m, const int64_t* off, int S,
+                      unsigned long long* counts, cudaStream_t s) {
+  if (m <= 0) return MSM_OK;
+  int64_t grid = (m + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (grid > cap) grid = cap;
+  kt_begin(KC_OTHER, s);
+  set_count_kernel<<<(int)grid, kThreads, 0, s>>>(pairs, m, off, S, counts);
+  kt_end(s);
+  MSM_LAUNCH("set_count_kernel");
+  return MSM_OK;
+}
 
 // Field layout of the strings: usable when every block fits 15 bits and the
 // blocks fit 8 words.  Returns the padded word count FP (even), or 0.
@@ -816,7 +1018,7 @@ int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
   GroupWs g = carve(ws, items);
   kt_begin(KC_BOUNDS, s);
   run_count_kernel<<<(unsigned)chunks, kThreads, 0, s>>>(b.keys, items, b.n, b.masks,
-                                                        g.cnt_start, g.cnt_end);
+                                                        b.start_bits, g.cnt_start, g.cnt_end);
   kt_end(s);
   MSM_LAUNCH("run_count_kernel");
   int rc = exclusive_scan_u32(g.cnt_start, g.off_start, chunks, g.scan_ws, nullptr, s);
@@ -825,7 +1027,7 @@ int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
   if (rc) return rc;
   kt_begin(KC_BOUNDS, s);
   run_write_kernel<<<(unsigned)chunks, kThreads, 0, s>>>(
-      b.keys, items, b.n, b.masks, g.off_start, g.off_end, g.starts, g.ends, chunks,
+      b.keys, items, b.n, b.masks, b.start_bits, g.off_start, g.off_end, g.starts, g.ends, chunks,
       g.cnt_start, g.ngroups);
   kt_end(s);
   MSM_LAUNCH("run_write_kernel");
@@ -872,32 +1074,56 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   a.cand = cand;
   a.cap = cap;
   a.count = count_dev;
-  int grid = num_sms() * 6;
+  a.X = b.X;
+  a.dtype = b.dtype;
+  a.dim = b.dim;
+  a.metric = b.metric;
+  a.eps = b.eps;
+  a.relS = 10.f * (float)dist::kU;
+  a.nrm = b.nrm;
+  a.kept = b.kept;
+  a.set_kept = b.set_kept;
+  a.set_off = b.set_off;
+  a.nsets = b.nsets;
+  const bool fuse = b.X != nullptr;
+  if (fuse && !b.kept) return set_error("fused recheck needs counters"), MSM_E_INVAL;
+  const int mb = b.min_blocks ? b.min_blocks : 4;
+  const int grid = num_sms() * (b.ctas_per_sm > 0 ? b.ctas_per_sm : 6);
   MSM_CUDA(cudaMemsetAsync(g.grab, 0, sizeof(unsigned), s));
   kt_begin(KC_CHECK, s);
   if (b.fields) {
+#define MSM_CHECK_FIELDS(P, U)                                                           \
+  if (!fuse) check_fields_kernel<P, U, false, 0><<<grid, kThreads, 0, s>>>(a, b.fields);   \
+  else if (mb == 2) check_fields_kernel<P, U, true, 2><<<grid, kThreads, 0, s>>>(a, b.fields); \
+  else if (mb == 5) check_fields_kernel<P, U, true, 5><<<grid, kThreads, 0, s>>>(a, b.fields); \
+  else check_fields_kernel<P, U, true, 4><<<grid, kThreads, 0, s>>>(a, b.fields)
     switch (b.FU) {  // words holding fields: ceil(k / 2)
-      case 1: check_fields_kernel<2, 1><<<grid, kThreads, 0, s>>>(a, b.fields); break;
-      case 2: check_fields_kernel<2, 2><<<grid, kThreads, 0, s>>>(a, b.fields); break;
-      case 3: check_fields_kernel<4, 3><<<grid, kThreads, 0, s>>>(a, b.fields); break;
-      case 4: check_fields_kernel<4, 4><<<grid, kThreads, 0, s>>>(a, b.fields); break;
-      case 5: check_fields_kernel<6, 5><<<grid, kThreads, 0, s>>>(a, b.fields); break;
-      case 6: check_fields_kernel<6, 6><<<grid, kThreads, 0, s>>>(a, b.fields); break;
-      case 7: check_fields_kernel<8, 7><<<grid, kThreads, 0, s>>>(a, b.fields); break;
-      case 8: check_fields_kernel<8, 8><<<grid, kThreads, 0, s>>>(a, b.fields); break;
+      case 1: MSM_CHECK_FIELDS(2, 1); break;
+      case 2: MSM_CHECK_FIELDS(2, 2); break;
+      case 3: MSM_CHECK_FIELDS(4, 3); break;
+      case 4: MSM_CHECK_FIELDS(4, 4); break;
+      case 5: MSM_CHECK_FIELDS(6, 5); break;
+      case 6: MSM_CHECK_FIELDS(6, 6); break;
+      case 7: MSM_CHECK_FIELDS(8, 7); break;
+      case 8: MSM_CHECK_FIELDS(8, 8); break;
       default: kt_end(s); return set_error("bad field word count"), MSM_E_INVAL;
     }
+#undef MSM_CHECK_FIELDS
     kt_end(s);
     MSM_LAUNCH("check_fields_kernel");
     return MSM_OK;
   }
+#define MSM_CHECK(WW)                                                     \
+  if (fuse) check_kernel<WW, true, 4><<<grid, kThreads, 0, s>>>(a);       \
+  else check_kernel<WW, false, 0><<<grid, kThreads, 0, s>>>(a)
   switch (b.W) {
-    case 1: check_kernel<1><<<grid, kThreads, 0, s>>>(a); break;
-    case 2: check_kernel<2><<<grid, kThreads, 0, s>>>(a); break;
-    case 3: check_kernel<3><<<grid, kThreads, 0, s>>>(a); break;
-    case 4: check_kernel<4><<<grid, kThreads, 0, s>>>(a); break;
+    case 1: MSM_CHECK(1); break;
+    case 2: MSM_CHECK(2); break;
+    case 3: MSM_CHECK(3); break;
+    case 4: MSM_CHECK(4); break;
     default: kt_end(s); return set_error("bad word count"), MSM_E_INVAL;
   }
+#undef MSM_CHECK
   kt_end(s);
   MSM_LAUNCH("check_kernel");
   return MSM_OK;

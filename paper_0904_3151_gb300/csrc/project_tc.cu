@@ -344,12 +344,17 @@ __global__ void project_fix_kernel(const void* X, int dtype, int64_t n, int dim,
                                    const uint64_t* fix,
                                    const unsigned long long* fix_count,
                                    int64_t fix_cap, uint64_t* strings,
-                                   unsigned long long* recompute) {
+                                   unsigned long long* recompute, unsigned* status) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int64_t m = (int64_t)*fix_count;
-  if (m > fix_cap) m = fix_cap;
+  if (m > fix_cap) {
+    // the queue overflowed: the strings are incomplete and the caller must
+    // project again on the CUDA-core path (status bit 1)
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, 2u);
+    return;
+  }
   const float m2 = (float)(2 * dim + 8) * 0x1.0p-24f;
   for (int64_t it = warp; it < m; it += nwarps) {
     const uint64_t e = fix[it];
@@ -452,7 +457,7 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
   p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
   uint64_t* fix = (uint64_t*)p; p += 8 * (size_t)fix_cap;
   unsigned long long* fix_count = (unsigned long long*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
-  *fell_back = false;
+  if (fell_back) *fell_back = false;
 
   MSM_CUDA(cudaMemsetAsync(fix_count, 0, 8, s));
   MSM_CUDA(cudaMemsetAsync(rnorm, 0, 4 * (size_t)rows, s));
@@ -504,6 +509,17 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
   kt_end(s);
   MSM_LAUNCH("project_tc_kernel");
 
+  if (!fell_back) {
+    // no host round trip: the fix-up reads the queue length on the device
+    // and reports an overflow in *status (bit 1) for the caller to act on
+    kt_begin(KC_PROJECT, s);
+    project_fix_kernel<<<num_sms() * 16, 256, 0, s>>>(X, dtype, n, dim, R, ell, W, xnorm, rnorm,
+                                                      fix, fix_count, fix_cap, strings,
+                                                      recompute, status);
+    kt_end(s);
+    MSM_LAUNCH("project_fix_kernel");
+    return MSM_OK;
+  }
   // queued bits; an overflowing queue means the tensor-core pass cannot be
   // completed from it, so the caller reruns the projection on the SIMT path
   unsigned long long cnt = 0;
@@ -523,7 +539,7 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
     if (grid2 > cap) grid2 = cap;
     kt_begin(KC_PROJECT, s);
     project_fix_kernel<<<grid2, 256, 0, s>>>(X, dtype, n, dim, R, ell, W, xnorm, rnorm, fix,
-                                              fix_count, fix_cap, strings, recompute);
+                                              fix_count, fix_cap, strings, recompute, status);
     kt_end(s);
     MSM_LAUNCH("project_fix_kernel");
   }

@@ -1,173 +1,15 @@
 // Step A8 (Sec. 4.1, last step): exact distance test of each candidate pair
 // in E, keeping Delta(x_i, x_j) <= eps (Def. 1.1, inclusive).
 //
-// Fast path (float): S = sum_c (x_ic - x_jc)^2, each lane of a 4-lane group
-// summing its share of coordinates with compensated (Kahan) summation, then
-// a 2-level shuffle tree.  Every term carries at most 3 roundings
-// (difference, square, and the compensated sum's 2u) and the tree adds at
-// most 3, so |S' - S| <= 8u S + O(u^2) with u = 2^-24.
-//   Euclidean: Delta = sqrt(S).
-//   Cosine (Eq. 2): from |x_i - x_j|^2 = |x_i|^2 + |x_j|^2 - 2 x_i.x_j,
-//     Delta = (S - (|x_i| - |x_j|)^2) / (2 |x_i| |x_j|), norms in double;
-//     used only when (|x_i| - |x_j|)^2 <= S / 2, so the subtraction at most
-//     doubles the relative error.
-// A comparison whose float-path distance lies within its error bound (plus
-// the rounding error of the double-precision reference) of eps is decided
-// again on the double-precision distance evaluated exactly as Eq. 2 (or the
-// Euclidean norm) with sequential fma over the coordinates.
-#include <cuda_bf16.h>
-
-#include "msm_internal.cuh"
+// The decision rule (float path with a derived error bound, double-precision
+// definition inside the margin) is in distance.cuh.
+#include "distance.cuh"
 
 namespace msm {
 namespace {
 
+using namespace dist;
 constexpr int kThreads = 256;
-constexpr double kU = 0x1.0p-24;
-
-__device__ __forceinline__ float ldx(const void* X, int dtype, int64_t idx) {
-  if (dtype == MSM_DT_BF16)
-    return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(X)[idx]);
-  return reinterpret_cast<const float*>(X)[idx];
-}
-
-// Distance in double precision, same operation order as the definition:
-// cosine 1 - dot / (sqrt(|x_i|^2) * sqrt(|x_j|^2)), Euclidean sqrt(sum t^2).
-__device__ double exact_distance(const void* X, int dtype, int64_t i,
-                                 int64_t j, int dim, int metric) {
-  const int64_t bi = i * dim, bj = j * dim;
-  if (metric == MSM_COSINE) {
-    double dot = 0.0, ni = 0.0, nj = 0.0;
-    for (int c = 0; c < dim; ++c)
-      dot = fma((double)ldx(X, dtype, bi + c), (double)ldx(X, dtype, bj + c), dot);
-    for (int c = 0; c < dim; ++c) {
-      double v = (double)ldx(X, dtype, bi + c);
-      ni = fma(v, v, ni);
-    }
-    for (int c = 0; c < dim; ++c) {
-      double v = (double)ldx(X, dtype, bj + c);
-      nj = fma(v, v, nj);
-    }
-    return 1.0 - dot / (sqrt(ni) * sqrt(nj));
-  }
-  double s = 0.0;
-  for (int c = 0; c < dim; ++c) {
-    double t = (double)ldx(X, dtype, bi + c) - (double)ldx(X, dtype, bj + c);
-    s = fma(t, t, s);
-  }
-  return sqrt(s);
-}
-
-// Float-path decision from S' (relative error <= relS) and the float row
-// norms (each within u of the true norm).  Everything here is float: the
-// FP64 pipe of this GPU is narrow, and a per-pair double evaluation made the
-// recheck FP64-bound.  Error of the cosine value (S' - T') / (2 n_i n_j):
-//   S' contributes <= 2 relS (S - T) because T <= S/2 is required;
-//   T' = (n_i' - n_j')^2 is off by <= 4 u |n_i' - n_j'| (n_i + n_j)
-//        + 8 u^2 (n_i + n_j)^2 + 2 u T' (rounded norms, square);
-//   the subtraction, product and division add <= 5 u more.
-// The double-precision reference itself is within (dim + 8) 2^-51 of the
-// true value.  Returns false when the float path cannot settle the
-// comparison (too close to eps) or cannot guarantee 4e-6 relative accuracy
-// of the reported distance (need_accuracy); the caller then evaluates the
-// distance by its definition in double precision.
-__device__ __forceinline__ bool decide_fast(float S, float ni, float nj,
-                                            int metric, int dim, float eps,
-                                            float relS, bool need_accuracy,
-                                            float* delta_out, bool* keep) {
-  const float u = 0x1.0p-24f;
-  float delta, rel, abs_err;
-  if (metric == MSM_COSINE) {
-    const float dn = ni - nj;
-    const float T = dn * dn;
-    if (T > 0.5f * S) return false;
-    const float num = S - T;
-    if (!(num > 0.f)) return false;
-    const float sn = ni + nj;
-    const float errT = 4.f * u * fabsf(dn) * sn + 8.f * u * u * sn * sn + 2.f * u * T;
-    delta = num / (2.f * ni * nj);
-    rel = 2.5f * relS + 8.f * u + errT / num;
-    abs_err = (float)(dim + 8) * 0x1.0p-51f;
-  } else {
-    delta = sqrtf(S);
-    rel = 0.5f * relS + 2.f * u + (float)(dim + 4) * 0x1.0p-52f;
-    abs_err = 0.f;
-  }
-  if (need_accuracy && rel > 4e-6f) return false;
-  const float margin = rel * delta + abs_err + 1e-30f;
-  if (fabsf(delta - eps) <= margin) return false;
-  *delta_out = delta;
-  *keep = delta <= eps;
-  return true;
-}
-
-// Decision for one pair: float path, else the double-precision definition.
-__device__ __forceinline__ double decide(const void* X, int dtype, int64_t i,
-                                         int64_t j, int dim, int metric,
-                                         float eps, float S, float ni, float nj,
-                                         float relS, bool need_accuracy,
-                                         bool* keep, bool* exact) {
-  float d32;
-  if (decide_fast(S, ni, nj, metric, dim, eps, relS, need_accuracy, &d32, keep)) {
-    *exact = false;
-    return (double)d32;
-  }
-  const double delta = exact_distance(X, dtype, i, j, dim, metric);
-  *exact = true;
-  *keep = delta <= (double)eps;
-  return delta;
-}
-
-// Sum of squared differences of rows i and j by the 8 lanes of a group.
-__device__ __forceinline__ void kahan_add(float v, float& acc, float& comp) {
-  const float y = v - comp;
-  const float s = acc + y;
-  comp = (s - acc) - y;
-  acc = s;
-}
-
-// Sum of squared differences of rows i and j by the G lanes of a group.
-// Float rows: each lane first issues 4 float4 loads per row, then adds, so
-// 8 independent 16-byte loads per lane are in flight (the kernel is bound
-// by gather latency).
-template <int G>
-__device__ __forceinline__ float group_sq_dist(const void* X, int dtype,
-                                               int64_t i, int64_t j, int dim,
-                                               int sl) {
-  float acc = 0.f, comp = 0.f;
-  const int64_t bi = i * dim, bj = j * dim;
-  if (dtype == MSM_DT_F32 && (dim & 3) == 0) {
-    const float4* xi = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + bi);
-    const float4* xj = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + bj);
-    const int n4 = dim / 4;
-    for (int c0 = sl; c0 < n4; c0 += 4 * G) {
-      float4 a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c4 = c0 + u * G;
-        a[u] = c4 < n4 ? __ldg(xi + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
-        b[u] = c4 < n4 ? __ldg(xj + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float t0 = a[u].x - b[u].x, t1 = a[u].y - b[u].y;
-        const float t2 = a[u].z - b[u].z, t3 = a[u].w - b[u].w;
-        kahan_add(__fmul_rn(t0, t0), acc, comp);
-        kahan_add(__fmul_rn(t1, t1), acc, comp);
-        kahan_add(__fmul_rn(t2, t2), acc, comp);
-        kahan_add(__fmul_rn(t3, t3), acc, comp);
-      }
-    }
-  } else {
-    for (int c = sl; c < dim; c += G) {
-      const float t = ldx(X, dtype, bi + c) - ldx(X, dtype, bj + c);
-      kahan_add(__fmul_rn(t, t), acc, comp);
-    }
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  return acc;
-}
 
 // 8 pairs per warp (4 lanes each), grid-stride over the candidates.
 __global__ void __launch_bounds__(kThreads)

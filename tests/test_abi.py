@@ -23,7 +23,8 @@ def L():
 def _declared():
     src = open(os.path.join(ROOT, "include", "msm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return set(re.findall(r"^\s*(?:int|int64_t|double|void|const char\*)\s+(msm_\w+)\s*\(", src, flags=re.M))
+    return set(re.findall(r"^\s*(?:int|int64_t|double|void\*?|const char\*)\s+(msm_\w+)\s*\(", src,
+                          flags=re.M))
 
 
 def test_every_declared_symbol_is_exported(L):

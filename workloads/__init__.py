@@ -38,15 +38,21 @@ class Workload:
     data_seed: int
     r_seed: int
     normalise: bool = True
+    # batched form: n_sets independent sets, sizes log-uniform in
+    # [set_min, set_max], n_clusters clusters in each set
+    n_sets: int = 1
+    set_min: int = 0
+    set_max: int = 0
 
     @property
     def masks(self) -> int:
         return math.comb(self.k, self.d)
 
 
-# The five evaluated configurations.  Index 0 is the small case that the CPU
-# oracle finishes in seconds; index 1 is the 1M x 128 workload the headline
-# throughput is quoted on.
+# The five evaluated configurations.  "small" is the case the CPU oracle
+# finishes in seconds; "scale" is the 1M x 128 workload the headline
+# throughput is quoted on.  For "batched" n is the expected total over the
+# sets (the actual sizes come from set_sizes).
 WORKLOADS = {
     "small": Workload("small", 20_000, 64, 50, 0.05, "cosine", 0.15, 64, 8, 4,
                       "f32", 1001, 2001),
@@ -54,6 +60,8 @@ WORKLOADS = {
                       128, 10, 6, "f32", 1002, 2002),
     "precision": Workload("precision", 4_000_000, 256, 4_000, 0.05,
                           "euclidean", 0.30, 128, 12, 8, "bf16", 1003, 2003),
+    "batched": Workload("batched", 9_600_000, 96, 20, 0.05, "cosine", 0.12, 64, 8, 4,
+                        "f32", 1004, 2004, n_sets=256, set_min=1_000, set_max=200_000),
     "learned": Workload("learned", 8_000_000, 128, 10_000, 0.05, "cosine",
                         0.10, 96, 8, 4, "bf16", 1005, 2005),
 }
@@ -91,6 +99,34 @@ def clustered_split(n_first: int, n_second: int, dim: int, n_clusters: int,
     n_first and the next n_second points of one draw."""
     X = clustered(n_first + n_second, dim, n_clusters, sigma, seed, normalise)
     return X[:n_first], X[n_first:]
+
+
+def set_sizes(n_sets: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """Sizes of the batched form's point sets: floor(exp(U[ln lo, ln hi]))."""
+    rng = np.random.default_rng(seed)
+    return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi), n_sets))).astype(np.int64)
+
+
+def clustered_sets(sizes, dim: int, n_clusters: int, sigma: float, seed: int,
+                   normalise: bool = True):
+    """Independent point sets, each a mixture of its own n_clusters centres
+    (drawn as in ``clustered`` from the stream [seed, s]), concatenated.
+    Returns (X float32 [sum(sizes)][dim], offsets int64 [len(sizes) + 1])."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    X = np.empty((int(off[-1]), dim), dtype=np.float32)
+    for s, m in enumerate(sizes):
+        if m == 0:
+            continue
+        rng = np.random.default_rng([seed, s])
+        centres = rng.uniform(-1.0, 1.0, size=(n_clusters, dim))
+        lab = rng.integers(0, n_clusters, size=int(m))
+        x = centres[lab] + sigma * rng.standard_normal((int(m), dim))
+        if normalise:
+            x /= np.linalg.norm(x, axis=1, keepdims=True)
+        X[off[s]:off[s + 1]] = x
+    return X, off
 
 
 def cluster_labels(n: int, n_clusters: int, seed: int, dim: int,
