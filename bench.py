@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the bf16, learned-projection and batched forms")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
+    ap.add_argument("--no-precision", action="store_true", help="skip the precision form")
     return ap.parse_args()
 
 
@@ -196,6 +197,83 @@ def run_batched(msm, steps, stream):
         "speedup_vs_plain": ms_p / ms_b, "tuning": tu, "cuda_graph": graph,
         "note": "all sets and groupings in one captured CUDA graph per step (radix segments "
                 "split at set boundaries, eps test fused into the pair check)"}
+
+
+def run_precision(msm, steps, stream, n_sample=400_000):
+    """Precision form: 4,000,000 x 256 vectors stored bf16, Euclidean eps=0.3,
+    l=128, k=12, d=8 (495 groupings).  The same values are also run stored as
+    float32 (projection on CUDA cores: 1 KB rows); both must give identical
+    strings and pairs (signs and eps decisions are those of the double-
+    precision definition).  Q: the smallest from 6 up whose missing ratio,
+    measured exhaustively among the pairs of a random point sample, is
+    <= 1e-6.  Distance error: reported float distances of sampled result
+    pairs against a float64 evaluation of the definition."""
+    import torch
+    wl = W.WORKLOADS["precision"]
+    Xf = torch.from_numpy(W.to_bf16_values(W.clustered(wl.n, wl.dim, wl.n_clusters, wl.sigma,
+                                                       wl.data_seed))).cuda()
+    Xb = Xf.to(torch.bfloat16)
+    cap = 700 * wl.n
+    g = torch.Generator(device="cuda").manual_seed(3)
+    perm = torch.randperm(wl.n, device="cuda", generator=g)[:n_sample]
+    mark = torch.zeros(wl.n, dtype=torch.bool, device="cuda")
+    mark[perm] = True
+    truth = msm.eps_count_exhaustive(Xf[perm].contiguous(), msm.EUCLIDEAN, wl.eps)
+
+    def step(X, Q):
+        return lambda: msm.eps_graph(X, msm.EUCLIDEAN, wl.eps, wl.ell, wl.k, wl.d, Q=Q,
+                                     seed=wl.r_seed, cand_capacity=cap)
+
+    def sampled_ratio(p):
+        found = int((mark[p >> 32] & mark[p & 0xFFFFFFFF]).sum().item())
+        return (truth - found) / max(1, truth)
+
+    ladder = []
+    for Q in (6, 7, 8):
+        p, _, _ = step(Xb, Q)()
+        r = sampled_ratio(p)
+        ladder.append({"Q": Q, "missing_ratio_sampled": r})
+        del p
+        if r <= 1e-6:
+            break
+
+    # order-independent comparison of the two pair multisets (no 2e9-element
+    # sort): counts, plain sums and sums of an odd-multiplier mix (int64 wraps)
+    def mix(p):
+        h = p * 0x9E3779B97F4A7C15 - 0x61C8864680B583EB
+        return p.numel(), int(p.sum().item()), int((h ^ (h >> 29)).sum().item())
+
+    res = {}
+    for name, X in (("f32", Xf), ("bf16", Xb)):
+        ms, (p, dv, st) = time_steps(step(X, Q), steps, stream)
+        res[name] = {"ms": ms, "st": st, "mix": mix(p)}
+        if name == "bf16":
+            sel = torch.randint(0, p.numel(), (min(p.numel(), 1 << 20),), device="cuda",
+                                generator=g)
+            pi, pj = p[sel] >> 32, p[sel] & 0xFFFFFFFF
+            d64 = (Xf[pi].double() - Xf[pj].double()).norm(dim=1)
+            rel = ((dv[sel].double() - d64).abs() / d64.clamp_min(1e-300)).max().item()
+            ratio = sampled_ratio(p)
+        del p, dv
+    st = res["bf16"]["st"]
+    out = {
+        "value": wl.n / (res["bf16"]["ms"] / 1000.0), "unit": UNIT,
+        "ms_per_step": res["bf16"]["ms"], "Q": Q, "pairs": st["count"],
+        "fp32_storage": {"value": wl.n / (res["f32"]["ms"] / 1000.0),
+                         "ms_per_step": res["f32"]["ms"],
+                         "kernel_ms": res["f32"]["st"]["kernel_ms"]},
+        "speedup_vs_fp32_storage": res["f32"]["ms"] / res["bf16"]["ms"],
+        "pairs_identical_to_fp32_storage": res["bf16"]["mix"] == res["f32"]["mix"],
+        "missing_ratio_sampled": ratio, "Q_ladder": ladder,
+        "missing_sample": f"{truth:,} true pairs among {n_sample:,} random points",
+        "signs_decided_in_double": st["proj_recompute"],
+        "signs_total": Q * wl.n * wl.ell,
+        "eps_decisions_in_double": st["dist_recompute"],
+        "max_rel_dist_error_vs_f64": rel, "kernel_ms": st["kernel_ms"],
+        "note": "bf16 storage: tcgen05 kind::f16 projection (R split into bf16 high+low), "
+                "recheck on bf16 rows; fp32 storage of the same values: CUDA-core projection"}
+    del res, Xf, Xb
+    return out
 
 
 def workload_desc(wl, n, Q):
@@ -513,6 +591,8 @@ def main():
                           ms, max(2, min(3, a.steps)), stream)
         if not a.no_batched:
             forms["batched"] = run_batched(msm, max(2, min(3, a.steps)), stream)
+        if not a.no_precision:
+            forms["precision"] = run_precision(msm, 2, stream)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
     cpu = None

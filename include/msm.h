@@ -113,8 +113,9 @@ typedef struct msm_params {
   int out_mode;      /* MSM_OUT_*                                       */
   int flags;         /* MSM_FLAG_*                                      */
   int group_bits;    /* grouping-key width 8..32; 0 = automatic         */
-  int check_min_blocks; /* tuning: register budget of the count-only pair
-                           check, as resident CTAs per SM: 2, 4 or 5;
+  int check_min_blocks; /* tuning: register budget of the pair check, as
+                           resident CTAs per SM: 2, 4 or 5 for count-only
+                           output (fused recheck), 6 or 8 otherwise;
                            0 = automatic                                  */
   int64_t cand_capacity; /* initial candidate buffer (pairs); 0 = auto */
   /* Optional projection features (learned form): when Y is non-NULL the

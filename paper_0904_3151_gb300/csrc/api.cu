@@ -406,9 +406,9 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
   }
   if (Sb < 1) Sb = 1;
   if (Sb > M) Sb = M;
+  const int mbk = tu.check_min_blocks;
   if (tu.check_ctas_per_sm < 0 || tu.check_ctas_per_sm > 16 ||
-      (tu.check_min_blocks != 0 && tu.check_min_blocks != 2 && tu.check_min_blocks != 4 &&
-       tu.check_min_blocks != 5))
+      !(mbk == 0 || mbk == 2 || mbk == 4 || mbk == 5 || mbk == 6 || mbk == 8))
     return set_error("invalid pair-check tuning"), MSM_E_INVAL;
 
   BlockLayout* dL = (BlockLayout*)sc.get(sizeof(BlockLayout));

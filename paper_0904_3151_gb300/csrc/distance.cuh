@@ -128,17 +128,47 @@ __device__ __forceinline__ void kahan_add(float v, float& acc, float& comp) {
   acc = s;
 }
 
+__device__ __forceinline__ void sq_diff_bf16x2(uint32_t a, uint32_t b, float& acc, float& comp) {
+  // two bf16 values per word: a bf16 is the high half of a float
+  const float t0 = __uint_as_float(a << 16) - __uint_as_float(b << 16);
+  const float t1 = __uint_as_float(a & 0xffff0000u) - __uint_as_float(b & 0xffff0000u);
+  kahan_add(__fmul_rn(t0, t0), acc, comp);
+  kahan_add(__fmul_rn(t1, t1), acc, comp);
+}
+
 // Sum of squared differences of rows i and j by the G lanes of a group.
-// Float rows: each lane first issues 4 float4 loads per row, then adds, so
-// 8 independent 16-byte loads per lane are in flight (the kernel is bound
-// by gather latency).
+// Each lane first issues 4 16-byte loads per row (float4, or 8 bf16 values),
+// then adds, so 8 independent loads per lane are in flight (the kernel is
+// bound by gather latency).  Rows that are not 16-byte aligned are read one
+// element at a time.
 template <int G>
 __device__ __forceinline__ float group_sq_dist(const void* X, int dtype,
                                                int64_t i, int64_t j, int dim,
                                                int sl) {
   float acc = 0.f, comp = 0.f;
   const int64_t bi = i * dim, bj = j * dim;
-  if (dtype == MSM_DT_F32 && (dim & 3) == 0) {
+  const bool al16 = (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+  if (dtype == MSM_DT_BF16 && (dim & 7) == 0 && al16) {
+    const uint4* xi = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(X) + bi);
+    const uint4* xj = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(X) + bj);
+    const int n8 = dim / 8;
+    for (int c0 = sl; c0 < n8; c0 += 4 * G) {
+      uint4 a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c8 = c0 + u * G;
+        a[u] = c8 < n8 ? __ldg(xi + c8) : make_uint4(0u, 0u, 0u, 0u);
+        b[u] = c8 < n8 ? __ldg(xj + c8) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sq_diff_bf16x2(a[u].x, b[u].x, acc, comp);
+        sq_diff_bf16x2(a[u].y, b[u].y, acc, comp);
+        sq_diff_bf16x2(a[u].z, b[u].z, acc, comp);
+        sq_diff_bf16x2(a[u].w, b[u].w, acc, comp);
+      }
+    }
+  } else if (dtype == MSM_DT_F32 && (dim & 3) == 0 && al16) {
     const float4* xi = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + bi);
     const float4* xj = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + bj);
     const int n4 = dim / 4;

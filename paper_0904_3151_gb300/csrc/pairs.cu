@@ -749,7 +749,10 @@ __global__ void __launch_bounds__(kThreads, MINB)
 check_fields_kernel(CheckArgs a, const uint32_t* fields) {
   __shared__ __align__(16) uint32_t sm_f[kThreads / 32][32][FP];
   __shared__ uint32_t sm_i[kThreads / 32][32];
-  __shared__ uint64_t sm_q[kThreads / 32][32];  // fused recheck queue
+  __shared__ uint64_t sm_q[kThreads / 32][32];       // fused recheck queue
+  __shared__ uint32_t sm_fr[kThreads / 32][32][FP];  // tile rows' fields
+  __shared__ uint32_t sm_ir[kThreads / 32][32];      // tile rows' points
+  __shared__ uint16_t sm_qs[kThreads / 32][1024];    // survivors: row << 5 | column
   // pair p of a group of <= 32 items, column by column: p = b(b-1)/2 + a
   __shared__ uint8_t tri_a[496], tri_b[496];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -847,8 +850,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
           unsigned long long b0 = 0;
           if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)__popc(bal));
           b0 = __shfl_sync(0xffffffffu, b0, 0) + __popc(bal & ((1u << lane) - 1u));
-          if (pass && b0 < (unsigned long long)a.cap)
-            a.cand[b0] = ((uint64_t)(ii < jj ? ii : jj) << 32) | (ii < jj ? jj : ii);
+          if (pass && b0 < (unsigned long long)a.cap) a.cand[b0] = ordered_pair(ii, jj);
         }
       }
       __syncwarp();
@@ -911,18 +913,61 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
           gpass |= (uint32_t)gaps_differ<FP, FU>(fa, sm_f[warp][c], gapf) << c;
       }
       gpass &= va ? colmask : 0u;
-      uint32_t passm = 0;
-      while (gpass) {
-        const int c = __ffs(gpass) - 1;
-        gpass &= gpass - 1;
-        if (fields_rest_ok<FP, FU>(fa, sm_f[warp][c], a.d, hashed, keepf)) {
-          const uint32_t ib = sm_i[warp][c];
-          if (replicates_ok_fields<FP>(a, fields, ia < ib ? ia : ib, ia < ib ? ib : ia))
-            passm |= 1u << c;
+      // Survivors of the gap test (~5 % of the pairs) take the Hamming, kept-
+      // block and replicate tests.  The replicate test reads earlier pools
+      // from global memory, so the survivors of the whole tile are queued
+      // once in shared memory and tested 32 at a time, one per lane: the
+      // loads of 32 pairs are in flight together instead of each lane
+      // walking its own survivors one dependent load after another.  Each
+      // round appends its passing pairs with one warp-aggregated atomic.
+      uint32_t cnt = __popc(gpass), incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total) {
+#pragma unroll
+        for (int w = 0; w < FP; ++w) sm_fr[warp][lane][w] = fa[w];
+        sm_ir[warp][lane] = ia;
+        uint32_t m = gpass, pos = incl - cnt;
+        while (m) {
+          const int c = __ffs(m) - 1;
+          m &= m - 1;
+          sm_qs[warp][pos++] = (uint16_t)(((uint32_t)lane << 5) | c);
+        }
+        for (uint32_t b0 = 0; b0 < total; b0 += 32) {
+          __syncwarp();
+          const uint32_t nb = min(32u, total - b0);
+          bool ok = false;
+          uint32_t ii = 0, jj = 0, r = 0, c = 0;
+          if ((uint32_t)lane < nb) {
+            const uint32_t e = sm_qs[warp][b0 + lane];
+            r = e >> 5;
+            c = e & 31u;
+            uint32_t fr[FP];
+#pragma unroll
+            for (int w = 0; w < FP; ++w) fr[w] = sm_fr[warp][r][w];
+            if (fields_rest_ok<FP, FU>(fr, sm_f[warp][c], a.d, hashed, keepf)) {
+              ii = sm_ir[warp][r];
+              jj = sm_i[warp][c];
+              ok = replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj, ii < jj ? jj : ii);
+            }
+          }
+          if constexpr (FUSE) {
+            fuse_one(a, ok, ii, jj, lane, sm_q[warp], acc);
+          } else {
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (bal) {
+              unsigned long long b1 = 0;
+              if (lane == 0) b1 = atomicAdd(a.count, (unsigned long long)__popc(bal));
+              b1 = __shfl_sync(0xffffffffu, b1, 0) + __popc(bal & ((1u << lane) - 1u));
+              if (ok && b1 < (unsigned long long)a.cap) a.cand[b1] = ordered_pair(ii, jj);
+            }
+          }
         }
       }
-      if constexpr (FUSE) fuse_mask(a, passm, ia, sm_i[warp], lane, sm_q[warp], acc);
-      else emit_mask(a, passm, ia, sm_i[warp], lane);
       __syncwarp();
     }
   }
@@ -1092,11 +1137,15 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   MSM_CUDA(cudaMemsetAsync(g.grab, 0, sizeof(unsigned), s));
   kt_begin(KC_CHECK, s);
   if (b.fields) {
-#define MSM_CHECK_FIELDS(P, U)                                                           \
-  if (!fuse) check_fields_kernel<P, U, false, 0><<<grid, kThreads, 0, s>>>(a, b.fields);   \
-  else if (mb == 2) check_fields_kernel<P, U, true, 2><<<grid, kThreads, 0, s>>>(a, b.fields); \
-  else if (mb == 5) check_fields_kernel<P, U, true, 5><<<grid, kThreads, 0, s>>>(a, b.fields); \
-  else check_fields_kernel<P, U, true, 4><<<grid, kThreads, 0, s>>>(a, b.fields)
+#define MSM_LAUNCH_CF(P, U, F, M) \
+  check_fields_kernel<P, U, F, M><<<grid, kThreads, 0, s>>>(a, b.fields)
+#define MSM_CHECK_FIELDS(P, U)                                  \
+  if (!fuse && b.min_blocks == 6) MSM_LAUNCH_CF(P, U, false, 6); \
+  else if (!fuse && b.min_blocks == 8) MSM_LAUNCH_CF(P, U, false, 8); \
+  else if (!fuse) MSM_LAUNCH_CF(P, U, false, 0);                \
+  else if (mb == 2) MSM_LAUNCH_CF(P, U, true, 2);               \
+  else if (mb == 5) MSM_LAUNCH_CF(P, U, true, 5);               \
+  else MSM_LAUNCH_CF(P, U, true, 4)
     switch (b.FU) {  // words holding fields: ceil(k / 2)
       case 1: MSM_CHECK_FIELDS(2, 1); break;
       case 2: MSM_CHECK_FIELDS(2, 2); break;
@@ -1109,6 +1158,7 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
       default: kt_end(s); return set_error("bad field word count"), MSM_E_INVAL;
     }
 #undef MSM_CHECK_FIELDS
+#undef MSM_LAUNCH_CF
     kt_end(s);
     MSM_LAUNCH("check_fields_kernel");
     return MSM_OK;
