@@ -95,48 +95,71 @@ __device__ __forceinline__ bool bit_at(const uint32_t* bits, int64_t i) {
   return (bits[i >> 5] >> (i & 31)) & 1u;
 }
 
-// Run boundary flags of flat position p whose offset in its segment (of
-// length n) is `local`; runs are equal K-block parts of the key (the key
-// shifted right by the segment's sub-key width sw) inside one point set
-// (sb: set starts, or NULL for a single set).
-__device__ __forceinline__ void run_flags(const uint32_t* keys, int64_t n,
-                                          int64_t p, int64_t local, int sw,
-                                          const uint32_t* sb, bool& start,
-                                          bool& end) {
-  uint32_t k = keys[p] >> sw;
-  bool head = (local == 0) || (keys[p - 1] >> sw) != k;
-  bool tail = (local == n - 1) || (keys[p + 1] >> sw) != k;
-  if (sb) {
-    head = head || bit_at(sb, local);
-    tail = tail || (local + 1 < n && bit_at(sb, local + 1));
+// Padded shared-memory slot of chunk position e (one pad word per 16), so
+// that a thread reading its 16 consecutive keys hits distinct banks.
+__device__ __forceinline__ int kslot(int e) { return e + (e >> 4); }
+constexpr int kStageWords = kChunk + 2 + (kChunk + 2) / 16 + 1;
+
+// Run boundary flags of the 16 consecutive positions p0 .. p0+15 of this
+// thread (bit j of *fs: a run of >= 2 starts at p0 + j; of *fe: one ends
+// there).  Runs are equal K-block parts of the key (the key shifted right by
+// the segment's sub-key width) inside one segment of n positions and one
+// point set (sb: set starts, or NULL for a single set).  The block's keys,
+// with one neighbour on each side, are first staged in shared memory by
+// coalesced loads.
+__device__ __forceinline__ void chunk_flags(const uint32_t* keys, int64_t items, int64_t n,
+                                            const MaskDesc* masks, const uint32_t* sb,
+                                            uint32_t* sk, uint32_t* fs_out,
+                                            uint32_t* fe_out) {
+  const int64_t b0 = (int64_t)blockIdx.x * kChunk;
+  for (int e = threadIdx.x; e < kChunk + 2; e += kThreads) {
+    const int64_t p = b0 - 1 + e;
+    sk[kslot(e)] = (p >= 0 && p < items) ? keys[p] : 0u;
   }
-  start = head && !tail;
-  end = tail && !head;
+  __syncthreads();
+  const int t0 = threadIdx.x * 16;
+  const int64_t p0 = b0 + t0;
+  uint32_t fs = 0, fe = 0;
+  int64_t local = p0 % n;
+  int64_t seg = p0 / n;
+  int sw = p0 < items ? masks[seg].sub_width : 0;
+  uint32_t prev = sk[kslot(t0)] >> sw, cur = sk[kslot(t0 + 1)] >> sw;
+  for (int j = 0; j < 16; ++j, ++local) {
+    if (local >= n) {  // entering the next segment (another kept-block set)
+      local -= n;
+      ++seg;
+      if (p0 + j < items) {
+        sw = masks[seg].sub_width;
+        cur = sk[kslot(t0 + j + 1)] >> sw;
+      }
+    }
+    const int64_t p = p0 + j;
+    const uint32_t next = sk[kslot(t0 + j + 2)] >> sw;
+    if (p < items) {
+      bool head = (local == 0) || prev != cur;
+      bool tail = (local == n - 1) || next != cur;
+      if (sb) {
+        head = head || bit_at(sb, local);
+        tail = tail || (local + 1 < n && bit_at(sb, local + 1));
+      }
+      fs |= (uint32_t)(head && !tail) << j;
+      fe |= (uint32_t)(tail && !head) << j;
+    }
+    prev = cur;
+    cur = next;
+  }
+  *fs_out = fs;
+  *fe_out = fe;
 }
 
 __global__ void run_count_kernel(const uint32_t* keys, int64_t items, int64_t n,
                                  const MaskDesc* masks, const uint32_t* sb,
                                  uint32_t* cnt_start,
                                  uint32_t* cnt_end) {
-  int64_t p0 = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * 16;
-  uint32_t cs = 0, ce = 0;
-  int64_t local = p0 % n;
-  int64_t seg = p0 / n;
-  int sw = p0 < items ? masks[seg].sub_width : 0;
-  for (int j = 0; j < 16; ++j, ++local) {
-    if (local >= n) {
-      local -= n;
-      ++seg;
-      if (p0 + j < items) sw = masks[seg].sub_width;
-    }
-    int64_t p = p0 + j;
-    if (p < items) {
-      bool s, e;
-      run_flags(keys, n, p, local, sw, sb, s, e);
-      cs += s;
-      ce += e;
-    }
-  }
+  __shared__ uint32_t sk[kStageWords];
+  uint32_t fs, fe;
+  chunk_flags(keys, items, n, masks, sb, sk, &fs, &fe);
+  uint32_t cs = __popc(fs), ce = __popc(fe);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     cs += __shfl_xor_sync(0xffffffffu, cs, o);
@@ -184,25 +207,10 @@ __global__ void run_write_kernel(const uint32_t* keys, int64_t items, int64_t n,
                                  uint32_t* ends, int64_t nchunks,
                                  const uint32_t* cnt_start, uint32_t* ngroups) {
   __shared__ uint32_t tmp[kThreads / 32];
-  int64_t p0 = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * 16;
-  uint32_t fs = 0, fe = 0;  // bit j: start / end at p0 + j
-  int64_t local = p0 % n;
-  int64_t seg = p0 / n;
-  int sw = p0 < items ? masks[seg].sub_width : 0;
-  for (int j = 0; j < 16; ++j, ++local) {
-    if (local >= n) {
-      local -= n;
-      ++seg;
-      if (p0 + j < items) sw = masks[seg].sub_width;
-    }
-    int64_t p = p0 + j;
-    if (p < items) {
-      bool s, e;
-      run_flags(keys, n, p, local, sw, sb, s, e);
-      fs |= (uint32_t)s << j;
-      fe |= (uint32_t)e << j;
-    }
-  }
+  __shared__ uint32_t sk[kStageWords];
+  const int64_t p0 = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * 16;
+  uint32_t fs, fe;  // bit j: start / end at p0 + j
+  chunk_flags(keys, items, n, masks, sb, sk, &fs, &fe);
   uint32_t os = block_excl(__popc(fs), tmp, nullptr) + off_start[blockIdx.x];
   uint32_t oe = block_excl(__popc(fe), tmp, nullptr) + off_end[blockIdx.x];
   for (int j = 0; j < 16; ++j) {
