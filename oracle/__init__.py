@@ -15,7 +15,8 @@ import subprocess
 
 import numpy as np
 
-from .bound import miss_bound, p_cosine, p_euclidean, solve_Q  # noqa: F401
+from .bound import (choose_params, e2lsh_p, miss_bound, p_cosine, p_euclidean,  # noqa: F401
+                    solve_Q)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "msm_oracle.c")
@@ -67,6 +68,13 @@ def lib():
         L.orc_eps_bruteforce.argtypes = [f64p, i64, i32, i32, ctypes.c_double,
                                          u64p, f64p, i64]
         L.orc_eps_bruteforce.restype = i64
+        L.orc_e2lsh_offsets.argtypes = [ctypes.c_uint64, i32, i32, f32p]
+        L.orc_project_e2lsh.argtypes = [f64p, i64, i32, f64p, i32, i32, f32p,
+                                        ctypes.c_double, i32, u64p]
+        L.orc_sym_pairs.argtypes = [u64p, i64, i32, i32, i32, u64p, i64]
+        L.orc_sym_pairs.restype = i64
+        L.orc_msm_sym.argtypes = [u64p, i64, i32, i32, i32, i32, i32, u64p, i64, i64p]
+        L.orc_msm_sym.restype = i64
         _lib = L
     return _lib
 
@@ -199,6 +207,69 @@ def eps_graph(X, R, ell: int, k: int, d: int, metric: int, eps: float):
     Returns (pairs, dist, info)."""
     S = project(X, R)
     E, st = msm(S, ell, k, d)
+    dv = dist(X, E, metric)
+    keep = dv <= float(np.float32(eps))
+    info = dict(st)
+    info["cand"] = int(E.shape[0])
+    info["type1"] = int((~keep).sum())
+    return E[keep], dv[keep], info
+
+
+# ------------------------------------------------------------ E2LSH symbols
+
+def e2lsh_offsets(seed: int, Q: int, ell: int) -> np.ndarray:
+    """Bucket offsets u in [0, 1), float32 [Q][ell] (counter-based, key
+    {seed, 2})."""
+    out = np.empty(Q * ell, dtype=np.float32)
+    lib().orc_e2lsh_offsets(ctypes.c_uint64(seed), Q, ell, _p(out, ctypes.c_float))
+    return out.reshape(Q, ell)
+
+
+def project_e2lsh(X, R, u, width: float, sw: int) -> np.ndarray:
+    """Symbol strings uint64 [Q][n][W], W = ceil(ell sw / 64): symbol c is the
+    low sw bits of floor(r_c^T x / width + u_c)."""
+    X = _f64(X)
+    R = _f64(R)
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    n, D = X.shape
+    Q, D2, ell = R.shape
+    assert D2 == D and u.shape == (Q, ell)
+    W = (ell * sw + 63) // 64
+    S = np.zeros((Q, n, W), dtype=np.uint64)
+    lib().orc_project_e2lsh(_p(X, ctypes.c_double), n, D, _p(R, ctypes.c_double), Q, ell,
+                            _p(u, ctypes.c_float), float(width), sw, _p(S, ctypes.c_uint64))
+    return S
+
+
+def sym_pairs(Sq, ell: int, sw: int, d: int) -> np.ndarray:
+    """Pairs of one pool with at most d differing symbols, by definition."""
+    Sq = np.ascontiguousarray(Sq, dtype=np.uint64)
+    n = Sq.shape[0]
+    out, _ = _grow_call(lambda b, cap: lib().orc_sym_pairs(
+        _p(Sq, ctypes.c_uint64), n, ell, sw, d, _p(b, ctypes.c_uint64), cap), 1 << 16)
+    return out
+
+
+def msm_sym(S, ell: int, sw: int, k: int, d: int):
+    """Blockwise MSM over symbol strings; returns (pairs, stats)."""
+    S = np.ascontiguousarray(S, dtype=np.uint64)
+    Q, n, _ = S.shape
+    st = np.zeros(3, dtype=np.int64)
+    out, _ = _grow_call(lambda b, cap: lib().orc_msm_sym(
+        _p(S, ctypes.c_uint64), n, ell, sw, k, d, Q, _p(b, ctypes.c_uint64), cap,
+        _p(st, ctypes.c_int64)), 1 << 16)
+    if int(st[2]) < 0:
+        raise ValueError("invalid MSM parameters")
+    return out, {"masks": int(st[0]), "checks": int(st[1]), "pairs": int(st[2])}
+
+
+def eps_graph_e2lsh(X, R, u, width: float, sw: int, ell: int, k: int, d: int, metric: int,
+                    eps: float):
+    """The method with E2LSH symbol strings: symbols for each replicate,
+    blockwise MSM over symbols with replicate de-duplication, exact distance
+    filter.  Returns (pairs, dist, info)."""
+    S = project_e2lsh(X, R, u, width, sw)
+    E, st = msm_sym(S, ell, sw, k, d)
     dv = dist(X, E, metric)
     keep = dv <= float(np.float32(eps))
     info = dict(st)

@@ -352,3 +352,149 @@ int64_t orc_eps_bruteforce(const double* X, int64_t n, int D, int metric,
         }
     return m;
 }
+
+/* ========================================================================
+ * E2LSH symbol strings (Sec. 3.1: LSH maps a vector to a string of
+ * integers; the Euclidean family of Datar et al. 2004, which Sec. 4.3 tunes
+ * by its width w).
+ * ---------------------------------------------------------------------- */
+
+/* Offsets of the buckets: u_{q,c} in [0, 1), one per (replicate, symbol):
+ * the top 24 bits of word 0 of Philox4x64-10 block q * ell + c under key
+ * {seed, 2}, times 2^-24 (exactly representable in float). */
+void orc_e2lsh_offsets(uint64_t seed, int Q, int ell, float* out) {
+    for (int64_t e = 0; e < (int64_t)Q * ell; ++e) {
+        uint64_t ctr[4] = {(uint64_t)e, 0, 0, 0}, key[2] = {seed, 2}, o[4];
+        orc_philox4x64_10(ctr, key, o);
+        out[e] = (float)((double)(o[0] >> 40) * 0x1.0p-24);
+    }
+}
+
+/* Symbol c of replicate q for point x: h = floor(t / width + u_{q,c}) with
+ * t = r_{q,c}^T x accumulated in double by sequential fma (as Eq. 3) and the
+ * division and addition done in double; the stored symbol is the low sw
+ * bits of h (two's complement).  Symbols are packed LSB first: symbol c
+ * occupies bits [c sw, (c + 1) sw) of the string. */
+void orc_project_e2lsh(const double* X, int64_t n, int D, const double* R, int Q,
+                       int ell, const float* u, double width, int sw, uint64_t* S) {
+    int W = (ell * sw + 63) / 64;
+    uint64_t mask = (sw >= 64) ? ~0ULL : ((1ULL << sw) - 1);
+    memset(S, 0, sizeof(uint64_t) * (size_t)Q * (size_t)n * (size_t)W);
+    for (int q = 0; q < Q; ++q)
+        for (int64_t i = 0; i < n; ++i)
+            for (int c = 0; c < ell; ++c) {
+                double t = 0.0;
+                for (int dd = 0; dd < D; ++dd)
+                    t = fma(X[i * D + dd], R[((size_t)q * D + dd) * ell + c], t);
+                double z = t / width + (double)u[(size_t)q * ell + c];
+                int64_t h = (int64_t)floor(z);
+                uint64_t sym = (uint64_t)h & mask;
+                int bit = c * sw;
+                S[((size_t)q * n + i) * W + (bit >> 6)] |= sym << (bit & 63);
+            }
+}
+
+/* Symbol c (sw bits) of a string. */
+static uint64_t sym_at(const uint64_t* s, int c, int sw) {
+    int bit = c * sw;
+    uint64_t v = s[bit >> 6] >> (bit & 63);
+    return sw >= 64 ? v : (v & ((1ULL << sw) - 1));
+}
+
+/* Symbol Hamming distance: number of symbols that differ. */
+static int mism(const uint64_t* a, const uint64_t* b, int ell, int sw) {
+    int h = 0;
+    for (int c = 0; c < ell; ++c) h += sym_at(a, c, sw) != sym_at(b, c, sw);
+    return h;
+}
+
+/* Eq. 1 over symbols, by definition: pairs i < j of one pool with at most
+ * d differing symbols, in increasing order; returns the count. */
+int64_t orc_sym_pairs(const uint64_t* S, int64_t n, int ell, int sw, int d,
+                      uint64_t* out, int64_t cap) {
+    int W = (ell * sw + 63) / 64;
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j)
+            if (mism(S + i * W, S + j * W, ell, sw) <= d) {
+                if (m < cap) out[m] = ((uint64_t)i << 32) | (uint64_t)j;
+                ++m;
+            }
+    return m;
+}
+
+/* Blockwise MSM (Sec. 2.2) over symbol strings: block b holds symbols
+ * [floor(b ell / k), floor((b + 1) ell / k)); a pair is inspected in every
+ * group of equal kept blocks, kept if at most d symbols differ, reported
+ * under the kept set made of its k - d lowest-index equal blocks, and only
+ * in the first replicate where it is within d (Appendix).  stats as
+ * orc_msm.  Returns the number of reported pairs, sorted ascending. */
+int64_t orc_msm_sym(const uint64_t* S, int64_t n, int ell, int sw, int k, int d, int Q,
+                    uint64_t* out, int64_t cap, int64_t* stats) {
+    int W = (ell * sw + 63) / 64;
+    int r = k - d;
+    if (d < 0 || r < 1 || k > ell || W > 4 || k > 64) return -1;
+    int blo[65];
+    for (int b = 0; b <= k; ++b) blo[b] = (int)((int64_t)b * ell / k);
+    orc_item* items = (orc_item*)malloc(sizeof(orc_item) * (size_t)(n > 0 ? n : 1));
+    int64_t masks = 0, checks = 0, m = 0;
+    int kept[64];
+    for (int q = 0; q < Q; ++q) {
+        const uint64_t* Sq = S + (size_t)q * n * W;
+        for (int j = 0; j < r; ++j) kept[j] = j;
+        do {
+            uint64_t K = 0;
+            for (int j = 0; j < r; ++j) K |= 1ULL << kept[j];
+            ++masks;
+            /* key: the string with the masked-out blocks' symbols cleared */
+            for (int64_t i = 0; i < n; ++i) {
+                memset(items[i].key, 0, sizeof(items[i].key));
+                for (int j = 0; j < r; ++j)
+                    for (int c = blo[kept[j]]; c < blo[kept[j] + 1]; ++c) {
+                        int bit = c * sw;
+                        items[i].key[bit >> 6] |= sym_at(Sq + i * W, c, sw) << (bit & 63);
+                    }
+                items[i].idx = (uint32_t)i;
+            }
+            g_cmp_words = W;
+            qsort(items, (size_t)n, sizeof(orc_item), cmp_item);
+            int64_t s = 0;
+            while (s < n) {
+                int64_t e = s + 1;
+                while (e < n && memcmp(items[e].key, items[s].key, sizeof(uint64_t) * W) == 0) ++e;
+                for (int64_t a = s; a < e; ++a)
+                    for (int64_t b = a + 1; b < e; ++b) {
+                        ++checks;
+                        uint32_t i = items[a].idx, jj = items[b].idx;
+                        if (i > jj) { uint32_t t = i; i = jj; jj = t; }
+                        const uint64_t* si = Sq + (size_t)i * W;
+                        const uint64_t* sj = Sq + (size_t)jj * W;
+                        if (mism(si, sj, ell, sw) > d) continue;
+                        uint64_t low = 0;
+                        int cnt = 0;
+                        for (int b2 = 0; b2 < k && cnt < r; ++b2) {
+                            int eq = 1;
+                            for (int c = blo[b2]; c < blo[b2 + 1]; ++c)
+                                if (sym_at(si, c, sw) != sym_at(sj, c, sw)) eq = 0;
+                            if (eq) { low |= 1ULL << b2; ++cnt; }
+                        }
+                        if (low != K) continue;
+                        int earlier = 0;
+                        for (int g = 0; g < q && !earlier; ++g) {
+                            const uint64_t* Sg = S + (size_t)g * n * W;
+                            if (mism(Sg + (size_t)i * W, Sg + (size_t)jj * W, ell, sw) <= d)
+                                earlier = 1;
+                        }
+                        if (earlier) continue;
+                        if (m < cap) out[m] = ((uint64_t)i << 32) | jj;
+                        ++m;
+                    }
+                s = e;
+            }
+        } while (next_combination(kept, r, k));
+    }
+    free(items);
+    if (out && cap > 0) qsort(out, (size_t)(m < cap ? m : cap), sizeof(uint64_t), cmp_u64);
+    if (stats) { stats[0] = masks; stats[1] = checks; stats[2] = m; }
+    return m;
+}

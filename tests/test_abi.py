@@ -5,6 +5,7 @@ import math
 import os
 import re
 
+import numpy as np
 import pytest
 
 import oracle
@@ -82,3 +83,18 @@ def test_solve_Q_rejects_bad_input(L):
     q = ctypes.c_int(0)
     assert L.msm_solve_Q(64, 4, 0.1, 0.0, ctypes.byref(q)) == -1
     assert L.msm_solve_Q(64, 4, 1.5, 1e-3, ctypes.byref(q)) == -1
+
+
+def test_choose_params_matches_oracle(L):
+    import paper_0904_3151_gb300 as msm
+    for n in (2, 3, 1000, 1024, 20000, 1 << 20, 10_000_000):
+        for eps in (0.0123, 0.05, 0.1, 0.15):
+            for S in (0.0, 0.5, 10.0, 1e4, 1e8, 3e10):
+                p = oracle.p_cosine(float(np.float32(eps)))
+                try:
+                    want = oracle.choose_params(n, p, 1e-6, S)
+                except ValueError:
+                    with pytest.raises(msm.MSMError):
+                        msm.choose_params(n, p, 1e-6, S)
+                    continue
+                assert msm.choose_params(n, p, 1e-6, S) == want, (n, eps, S)

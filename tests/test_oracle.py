@@ -396,3 +396,32 @@ def test_eps_bruteforce_inclusive_boundary():
     Xc = np.array([[1.0, 0.0], [0.0, 2.0], [-1.0, 0.0]])
     got, dv = oracle.eps_bruteforce(Xc, COS, 1.0)      # orthogonal: exactly 1
     assert _pairs_set(got) == {(0, 1), (1, 2)}
+
+
+# ------------------------------------------------ Sec. 4.3 parameter rule
+
+def test_choose_params_hand_worked():
+    """n = 1024 -> l = 2 * 10 = 20; p = 0.1, gamma = 1e-6, S = 1e6 -> the
+    replicate limit is 24.  P(Binom(20, 0.1) <= 1) = 0.9^20 + 2 * 0.9^19 =
+    0.39175 -> Q = ceil(ln 1e-6 / ln 0.60825) = 28 > 24; P(<= 2) adds
+    190 * 0.01 * 0.9^18 = 0.28518 -> 0.67693 -> Q = ceil(13.8155 / 1.1299)
+    = 13.  So d = 2, k = 4, Q = 13."""
+    assert oracle.choose_params(1024, 0.1, 1e-6, 1e6) == (20, 4, 2, 13)
+
+
+def test_choose_params_halves_l_when_no_output():
+    """S < 1: l = 10, limit 5.  P(Binom(10, 0.1) <= 2) = 0.92981 ->
+    Q = ceil(13.8155 / 2.6565) = 6 > 5; P(<= 3) = 0.98720 -> Q = 4."""
+    assert oracle.choose_params(1024, 0.1, 1e-6, 0.5) == (10, 6, 3, 4)
+
+
+@pytest.mark.parametrize("n,p,S", [(5000, 0.12, 1e5), (1 << 20, 0.1436, 5e8),
+                                   (123457, 0.05, 10.0), (3, 0.2, 2.0)])
+def test_choose_params_is_minimal(n, p, S):
+    ell, k, d, Q = oracle.choose_params(n, p, 1e-6, S)
+    assert ell == min(256, 2 * math.ceil(math.log2(n)) // (1 if S >= 1 else 2))
+    assert k == (2 * d if d else 1)
+    limit = min(24, max(math.ceil(30 * S / n), 5))
+    assert Q <= limit and Q == oracle.solve_Q(ell, d, p, 1e-6)
+    if d > 0:  # one mismatch fewer needs more replicates than allowed
+        assert oracle.solve_Q(ell, d - 1, p, 1e-6) > limit
