@@ -276,6 +276,69 @@ def run_precision(msm, steps, stream, n_sample=400_000):
     return out
 
 
+def run_lsh_d0(msm, X, wl, n, truth, steps, stream, Q=300, gamma=1e-6):
+    """The paper's "LSH" variant (Sec. 5.1): the same method with d = 0 (exact
+    string match), Q = 300 replicates fixed, and the string length set to
+    the longest l whose Sec. 4.2 bound (1 - (1 - p)^l)^Q is <= gamma."""
+    p = msm.collision_p(msm.COSINE, wl.eps)
+    ell = 1
+    while ell < 64 and msm.miss_bound(ell + 1, 0, p, Q) <= gamma:
+        ell += 1
+    k = (ell + 14) // 15            # blocks of <= 15 bits (all kept when d = 0)
+
+    def step():
+        return msm.eps_graph(X, msm.COSINE, wl.eps, ell, k, 0, Q=Q, seed=wl.r_seed + 7,
+                             out_mode=msm.OUT_PAIRS, cand_capacity=600 * n)
+    step()
+    ms, (pr, _, st) = time_steps(step, steps, stream)
+    del pr
+    return {"value": n / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms, "Q": Q, "ell": ell,
+            "k": k, "d": 0, "missing_ratio": (truth - st["count"]) / max(1, truth),
+            "pairs": st["count"], "checks": st["checks"], "cand": st["cand"],
+            "kernel_ms": st["kernel_ms"],
+            "note": "Sec. 5.1 LSH variant: d = 0, Q = 300, l the longest meeting the bound "
+                    "for gamma = 1e-6 at the radius"}
+
+
+def run_auto_params(msm, X, wl, n, truth, steps, stream, gamma=1e-6):
+    """Automatic parameters (Sec. 4.3): l, k, d and Q from the paper's rule
+    applied to a sampled output-size estimate, on the scale workload."""
+    def step():
+        return msm.eps_graph(X, msm.COSINE, wl.eps, 0, 0, 0, Q=0, miss_ratio=gamma,
+                             seed=wl.r_seed + 11, out_mode=msm.OUT_PAIRS,
+                             cand_capacity=600 * n)
+    step()
+    ms, (pr, _, st) = time_steps(step, steps, stream)
+    del pr
+    return {"value": n / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms,
+            "ell": st["ell"], "k": st["k"], "d": st["d"], "Q": st["Q"], "S_est": st["S_est"],
+            "missing_ratio": (truth - st["count"]) / max(1, truth), "pairs": st["count"],
+            "checks": st["checks"],
+            "note": "Sec. 4.3 rule: l = 2 ceil(log2 n), replicate budget min(24, max(30 S/n, 5)), "
+                    "smallest d meeting gamma = 1e-6 by the bound, k = 2d"}
+
+
+def run_output_sensitivity(msm, wl, Q, stream, sizes=(125_000, 250_000, 500_000, 1_000_000)):
+    """Sec. 5.4 / Fig. 7: time per 10,000 output pairs as n grows (same
+    cluster size, so the output grows with n)."""
+    import torch
+    rows = []
+    for n in sizes:
+        X = torch.from_numpy(W.clustered(n, wl.dim, max(1, n * wl.n_clusters // wl.n),
+                                         wl.sigma, wl.data_seed + n)).cuda()
+
+        def step():
+            return msm.eps_graph(X, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=Q,
+                                 seed=wl.r_seed, out_mode=msm.OUT_PAIRS,
+                                 cand_capacity=600 * n)
+        step()
+        ms, (pr, _, st) = time_steps(step, 2, stream)
+        rows.append({"n": n, "ms": ms, "pairs": st["count"],
+                     "ms_per_10k_pairs": ms / max(1, st["count"]) * 1e4})
+        del pr, X
+    return rows
+
+
 def workload_desc(wl, n, Q):
     return (f"scale: n={n:,} fp32 vectors, dim={wl.dim}, {wl.n_clusters:,} Gaussian clusters "
             f"(sigma={wl.sigma}, centres U[-1,1]), unit-normalised, cosine eps={wl.eps}; "
@@ -593,6 +656,9 @@ def main():
             forms["batched"] = run_batched(msm, max(2, min(3, a.steps)), stream)
         if not a.no_precision:
             forms["precision"] = run_precision(msm, 2, stream)
+        forms["lsh_d0"] = run_lsh_d0(msm, X, wl, n, missing["truth_pairs"], 2, stream)
+        forms["auto_params"] = run_auto_params(msm, X, wl, n, missing["truth_pairs"], 2, stream)
+        forms["output_sensitivity"] = run_output_sensitivity(msm, wl, Q, stream)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
     cpu = None

@@ -58,6 +58,10 @@ extern "C" {
 #define MSM_OUT_PAIRS 1      /* pairs only (dist = NULL) */
 #define MSM_OUT_COUNT 2      /* count only (pairs = dist = NULL) */
 
+/* ---- string families (msm_params.hash) ---- */
+#define MSM_HASH_SIGN 0  /* sign random projection, Eq. 3 (1 bit per symbol) */
+#define MSM_HASH_E2LSH 1 /* E2LSH symbols floor(r^T x / width + u) (Datar et al.) */
+
 /* ---- flags ---- */
 #define MSM_FLAG_CANONICAL 1 /* sort output pairs ascending (i, then j) */
 #define MSM_FLAG_SIMT_PROJECTION 2 /* project on CUDA cores, not tcgen05 */
@@ -100,11 +104,17 @@ typedef struct msm_stats {
    * 7 other (norms, generator, canonical sort). */
   float kernel_ms[8];
   int64_t kernel_launches[8];
+  /* String geometry used (chosen by the Sec. 4.3 rule when msm_params.ell
+   * was 0) and that rule's output-size estimate S (-1 when not estimated). */
+  int ell, k, d, reserved;
+  double S_est;
 } msm_stats;
 
 /* Parameters of msm_eps_graph. */
 typedef struct msm_params {
-  int ell;  /* string length in bits (Sec. 3.2)                         */
+  int ell;  /* string length in bits (Sec. 3.2); 0 = automatic: ell, k,
+               d and Q from the Sec. 4.3 rule (msm_choose_params) on an
+               output-size estimate (msm_estimate_output, 2^22 samples)  */
   int k;    /* blocks per string (Sec. 2.2)                             */
   int d;    /* Hamming threshold = masked blocks per grouping (Sec. 2.2) */
   int Q;    /* replicates; 0 = smallest Q meeting miss_ratio (Sec. 4.3) */
@@ -127,6 +137,15 @@ typedef struct msm_params {
   /* Tuning (results never depend on these; 0 = automatic): */
   int masks_per_batch;   /* kept-block sets grouped per sort batch         */
   int check_ctas_per_sm; /* pair-check grid, CTAs per SM (1..16)           */
+  /* String family.  MSM_HASH_E2LSH: ell counts symbols of symbol_bits bits
+   * (2 or 4; 0 = 4), the low bits of floor(r^T x / width + u) with R drawn
+   * as for Eq. 3 and u by msm_e2lsh_offsets from `seed`; width is the
+   * bucket width in the units of X (0 = 4 radii, or the Sec. 4.3 rule when
+   * ell == 0); d counts differing symbols; the bound uses msm_e2lsh_p at
+   * the radius (Euclidean eps, or sqrt(2 eps) for cosine on unit rows). */
+  int hash;
+  int symbol_bits;
+  float width;
 } msm_params;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -154,6 +173,58 @@ double msm_miss_bound(int ell, int d, double p, int Q);
 /* Sec. 4.3: smallest Q >= 1 whose bound is <= gamma, written to *Q.
  * MSM_E_INVAL if gamma <= 0, p outside [0, 1), or no Q <= 2^24 suffices. */
 int msm_solve_Q(int ell, int d, double p, double gamma, int* Q);
+
+/* Sec. 4.3 parameter rule (host arithmetic).  Given n, the non-collision
+ * probability p at the radius (msm_collision_p), gamma and an estimate S of
+ * the output size:
+ *   ell = 2 ceil(log2 n) (halved when S < 1), at most 256;
+ *   replicate budget Qmax = min(24, max(ceil(30 S / n), 5));
+ *   d = the smallest d >= 0 whose bound-minimal Q (msm_solve_Q) is <= Qmax;
+ *   k = max(2 d, 1): the fewest blocks for which k - d blocks hold half of
+ *   the string, log2 n letters;
+ *   Q = that minimal Q.
+ * MSM_E_INVAL if no d with k <= min(ell, 32) meets the budget. */
+int msm_choose_params(int64_t n, double p, double gamma, double S, int* ell,
+                      int* k, int* d, int* Q);
+
+/* Sec. 4.3 output-size estimate: S = (pairs within eps among `samples`
+ * uniformly random pairs i != j) / samples * n (n - 1) / 2.  Pair t is
+ * drawn from block t of Philox4x64-10 with key {seed, 1}: i = w0 mod n,
+ * j = w1 mod (n - 1), then j += 1 if j >= i.  X: device [n][dim].
+ * Synchronises. */
+int msm_estimate_output(const void* X, int64_t n, int dim, int dtype,
+                        int metric, float eps, int64_t samples,
+                        uint64_t seed, double* S, void* stream);
+
+/* E2LSH (Sec. 3.1; Datar et al. 2004): non-collision probability of one
+ * symbol for a pair at distance c when the bucket width is w c:
+ * 2 Phi(-w) + 2 / (sqrt(2 pi) w) (1 - exp(-w^2 / 2)).  -1 if w <= 0. */
+double msm_e2lsh_p(double w);
+
+/* E2LSH bucket offsets, `count` floats in [0, 1) to device `out`: element e
+ * is (w0 >> 40) 2^-24 with w0 word 0 of Philox4x64-10 block e under key
+ * {seed, 2}.  Asynchronous. */
+int msm_e2lsh_offsets(uint64_t seed, int64_t count, float* out, void* stream);
+
+/* E2LSH symbol strings: symbol c of replicate q for row i is the low
+ * symbol_bits bits (two's complement) of h = floor(t / width + u[q][c]),
+ * t = r_{q,c}^T x_i; packed LSB first, symbol c at bits [c sb, (c+1) sb)
+ * of strings [Q][n][ceil(ell sb / 64)] (device, caller-owned).  Every h is
+ * the one of the double-precision evaluation of that expression with t by
+ * sequential fma.  R: device [Q][dim][ell] float; u: device [Q][ell].
+ * recomputed (optional host): symbols settled in double.  Synchronises. */
+int msm_project_e2lsh(const void* X, int64_t n, int dim, int dtype,
+                      const float* R, const float* u, float width, int ell,
+                      int Q, int symbol_bits, uint64_t* strings,
+                      int64_t* recomputed, void* stream);
+
+/* msm_enumerate over symbol strings of symbol_bits (1, 2 or 4) bits: ell
+ * counts symbols, blocks are groups of whole symbols, d counts differing
+ * symbols.  Synchronises. */
+int msm_enumerate_symbols(const uint64_t* strings, int64_t n, int ell,
+                          int symbol_bits, int k, int d, int Q, int flags,
+                          const msm_allocator* alloc, msm_pairs* out,
+                          msm_stats* stats, void* stream);
 
 /* Step A0' (Sec. 3.2: R has i.i.d. N(0, 1) entries).  Writes `count`
  * standard normal floats to device `out`: element e comes from block e/4 of

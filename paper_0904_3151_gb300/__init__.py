@@ -19,12 +19,14 @@ from ._lib import Allocator, Pairs, Params, Stats
 
 __all__ = ["MSMError", "gaussian", "project", "enumerate_pairs", "recheck",
            "eps_graph", "enumerate_sets", "eps_graph_sets", "Plan", "autotune",
-           "eps_count_exhaustive", "collision_p", "miss_bound",
+           "eps_count_exhaustive", "collision_p", "miss_bound", "choose_params",
+           "estimate_output",
            "solve_Q", "unpack_pairs", "COSINE", "EUCLIDEAN", "lib"]
 
 COSINE, EUCLIDEAN = 0, 1
 DT_F32, DT_BF16 = 0, 1
 OUT_PAIRS_DIST, OUT_PAIRS, OUT_COUNT = 0, 1, 2
+HASH_SIGN, HASH_E2LSH = 0, 1
 FLAG_CANONICAL = 1
 FLAG_SIMT_PROJECTION = 2
 
@@ -158,7 +160,7 @@ def recheck(X: torch.Tensor, cand: torch.Tensor, metric, eps: float):
 
 
 def _params(ell, k, d, Q, seed, R, Y, n, out_mode, canonical, simt_projection, group_bits,
-            cand_capacity, tuning=None):
+            cand_capacity, tuning=None, e2lsh=None):
     p = Params()
     p.ell, p.k, p.d, p.Q = ell, k, d, Q
     p.seed = seed
@@ -173,6 +175,10 @@ def _params(ell, k, d, Q, seed, R, Y, n, out_mode, canonical, simt_projection, g
     for key, v in (tuning or {}).items():
         assert key in ("masks_per_batch", "check_ctas_per_sm", "check_min_blocks"), key
         setattr(p, key, int(v))
+    if e2lsh is not None:
+        p.hash = HASH_E2LSH
+        p.symbol_bits = int(e2lsh.get("symbol_bits", 4))
+        p.width = float(e2lsh.get("width", 0.0))
     return p
 
 
@@ -180,10 +186,13 @@ def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
               Q: int = 0, miss_ratio: float = 1e-6, R: torch.Tensor | None = None,
               seed: int = 0, out_mode: int = OUT_PAIRS_DIST, canonical: bool = False,
               group_bits: int = 0, cand_capacity: int = 0, simt_projection: bool = False,
-              Y: torch.Tensor | None = None, device=None, tuning: dict | None = None):
+              Y: torch.Tensor | None = None, device=None, tuning: dict | None = None,
+              e2lsh: dict | None = None):
     """The whole method.  X may be a CUDA tensor or a (pinned) CPU tensor,
     which the library copies in.  With Y (CUDA [n][dim_y], e.g. learned
-    features) the strings come from Y while the recheck uses X.  ``tuning``
+    features) the strings come from Y while the recheck uses X.  ``e2lsh``
+    (dict with symbol_bits, width) selects E2LSH symbol strings of ell
+    symbols (d then counts differing symbols).  ``tuning``
     sets launch knobs of msm_params (masks_per_batch, check_ctas_per_sm,
     check_min_blocks); results do not depend on them.
     Returns (pairs, dist, stats)."""
@@ -191,7 +200,7 @@ def eps_graph(X: torch.Tensor, metric, eps: float, ell: int, k: int, d: int,
     n, dim = X.shape
     dev = X.device if X.is_cuda else torch.device(device or "cuda")
     p = _params(ell, k, d, Q, seed, R, Y, n, out_mode, canonical, simt_projection, group_bits,
-                cand_capacity, tuning)
+                cand_capacity, tuning, e2lsh)
     A = _TorchAllocator(dev)
     out = Pairs()
     st = Stats()
@@ -435,6 +444,77 @@ def eps_count_exhaustive(X: torch.Tensor, metric, eps: float) -> int:
                                           _metric(metric), ctypes.c_float(eps), ctypes.byref(c),
                                           _stream()), "msm_eps_count_exhaustive")
     return c.value
+
+
+def e2lsh_p(w: float) -> float:
+    """Non-collision probability of one E2LSH symbol at bucket width w times
+    the distance (Datar et al.)."""
+    return lib().msm_e2lsh_p(float(w))
+
+
+def e2lsh_offsets(seed: int, count: int, device=None) -> torch.Tensor:
+    out = torch.empty(count, dtype=torch.float32, device=device or "cuda")
+    _check(lib().msm_e2lsh_offsets(ctypes.c_uint64(seed), count, ctypes.c_void_p(out.data_ptr()),
+                                   _stream()), "msm_e2lsh_offsets")
+    return out
+
+
+def project_e2lsh(X: torch.Tensor, R: torch.Tensor, u: torch.Tensor, width: float,
+                  symbol_bits: int, return_recomputed: bool = False):
+    """E2LSH symbol strings int64 [Q][n][W] (W = ceil(ell * symbol_bits / 64))."""
+    assert X.is_cuda and X.is_contiguous() and R.is_cuda and R.is_contiguous() and u.is_cuda
+    n, dim = X.shape
+    Q, D2, ell = R.shape
+    assert D2 == dim and u.numel() == Q * ell
+    Wd = (ell * symbol_bits + 63) // 64
+    S = torch.empty((Q, n, Wd), dtype=torch.int64, device=X.device)
+    rec = ctypes.c_int64(0)
+    _check(lib().msm_project_e2lsh(ctypes.c_void_p(X.data_ptr()), n, dim, _dtype(X),
+                                   ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                   ctypes.c_float(width), ell, Q, symbol_bits,
+                                   ctypes.c_void_p(S.data_ptr()), ctypes.byref(rec), _stream()),
+           "msm_project_e2lsh")
+    return (S, rec.value) if return_recomputed else S
+
+
+def enumerate_symbols(strings: torch.Tensor, ell: int, symbol_bits: int, k: int, d: int,
+                      canonical: bool = False):
+    """enumerate_pairs over symbol strings (ell symbols of symbol_bits bits)."""
+    assert strings.is_cuda and strings.is_contiguous() and strings.dim() == 3
+    Q, n, Wd = strings.shape
+    assert Wd == (ell * symbol_bits + 63) // 64
+    A = _TorchAllocator(strings.device)
+    out = Pairs()
+    st = Stats()
+    _check(lib().msm_enumerate_symbols(ctypes.c_void_p(strings.data_ptr()), n, ell, symbol_bits,
+                                       k, d, Q, FLAG_CANONICAL if canonical else 0,
+                                       ctypes.byref(A.struct), ctypes.byref(out),
+                                       ctypes.byref(st), _stream()), "msm_enumerate_symbols")
+    return A.take(out.pairs, out.count, torch.int64), st.as_dict()
+
+
+def choose_params(n: int, p: float, gamma: float, S: float):
+    """Sec. 4.3 parameter rule: (ell, k, d, Q) for n points, non-collision
+    probability p at the radius, missing-ratio bound gamma and output-size
+    estimate S."""
+    e, k, d, Q = (ctypes.c_int() for _ in range(4))
+    _check(lib().msm_choose_params(int(n), ctypes.c_double(p), ctypes.c_double(gamma),
+                                   ctypes.c_double(S), ctypes.byref(e), ctypes.byref(k),
+                                   ctypes.byref(d), ctypes.byref(Q)), "msm_choose_params")
+    return e.value, k.value, d.value, Q.value
+
+
+def estimate_output(X: torch.Tensor, metric, eps: float, samples: int = 1 << 22,
+                    seed: int = 0) -> float:
+    """Sec. 4.3 output-size estimate from `samples` random pairs."""
+    assert X.is_cuda and X.is_contiguous() and X.dim() == 2
+    n, dim = X.shape
+    S = ctypes.c_double()
+    _check(lib().msm_estimate_output(ctypes.c_void_p(X.data_ptr()), n, dim, _dtype(X),
+                                     _metric(metric), ctypes.c_float(eps), int(samples),
+                                     ctypes.c_uint64(seed), ctypes.byref(S), _stream()),
+           "msm_estimate_output")
+    return S.value
 
 
 def collision_p(metric, eps: float) -> float:

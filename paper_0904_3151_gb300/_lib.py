@@ -32,7 +32,9 @@ class Stats(ctypes.Structure):
                 ("cand", ctypes.c_int64), ("type1", ctypes.c_int64),
                 ("proj_recompute", ctypes.c_int64), ("dist_recompute", ctypes.c_int64),
                 ("overflow_retries", ctypes.c_int64), ("ms", ctypes.c_float * 8),
-                ("kernel_ms", ctypes.c_float * 8), ("kernel_launches", ctypes.c_int64 * 8)]
+                ("kernel_ms", ctypes.c_float * 8), ("kernel_launches", ctypes.c_int64 * 8),
+                ("ell", ctypes.c_int), ("k", ctypes.c_int), ("d", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("S_est", ctypes.c_double)]
 
     PHASES = ["norms_R", "project", "group_sort", "group_bounds", "group_check",
               "recheck", "canonical", "total"]
@@ -40,7 +42,7 @@ class Stats(ctypes.Structure):
                "pair_check", "recheck", "other"]
 
     def as_dict(self):
-        skip = ("ms", "kernel_ms", "kernel_launches")
+        skip = ("ms", "kernel_ms", "kernel_launches", "reserved")
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in skip}
         d["ms"] = {k: float(v) for k, v in zip(self.PHASES, self.ms)}
         d["kernel_ms"] = {k: float(v) for k, v in zip(self.KERNELS, self.kernel_ms)}
@@ -54,7 +56,8 @@ class Params(ctypes.Structure):
                 ("flags", ctypes.c_int), ("group_bits", ctypes.c_int),
                 ("check_min_blocks", ctypes.c_int), ("cand_capacity", ctypes.c_int64),
                 ("Y", ctypes.c_void_p), ("dim_y", ctypes.c_int), ("dtype_y", ctypes.c_int),
-                ("masks_per_batch", ctypes.c_int), ("check_ctas_per_sm", ctypes.c_int)]
+                ("masks_per_batch", ctypes.c_int), ("check_ctas_per_sm", ctypes.c_int),
+                ("hash", ctypes.c_int), ("symbol_bits", ctypes.c_int), ("width", ctypes.c_float)]
 
 
 # Every symbol include/msm.h declares, with its ctypes signature.
@@ -68,6 +71,24 @@ SIGNATURES = {
     "msm_solve_Q": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_int)]),
     "msm_gaussian": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, vp, vp]),
+    "msm_e2lsh_p": (ctypes.c_double, [ctypes.c_double]),
+    "msm_e2lsh_offsets": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, vp, vp]),
+    "msm_project_e2lsh": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, vp,
+                                         ctypes.c_float, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         vp, i64p, vp]),
+    "msm_enumerate_symbols": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.POINTER(Allocator),
+                                             ctypes.POINTER(Pairs), ctypes.POINTER(Stats), vp]),
+    "msm_choose_params": (ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "msm_estimate_output": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_float, ctypes.c_int64,
+                                           ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                           vp]),
     "msm_project": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, ctypes.c_uint64,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, i64p, vp]),
     "msm_enumerate": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,

@@ -185,14 +185,15 @@ void Scratch::release(void* p) {
 }
 
 // ------------------------------------------------------------------ layout
-BlockLayout make_layout(int ell, int k) {
+BlockLayout make_layout(int ell_sym, int k, int sw) {
   BlockLayout L;
   memset(&L, 0, sizeof(L));
-  L.ell = ell;
+  L.ell = ell_sym * sw;
   L.k = k;
-  L.W = (ell + 63) / 64;
+  L.sw = sw;
+  L.W = (L.ell + 63) / 64;
   for (int b = 0; b < k; ++b) {
-    int lo = (int)((int64_t)b * ell / k), hi = (int)((int64_t)(b + 1) * ell / k);
+    int lo = sw * (int)((int64_t)b * ell_sym / k), hi = sw * (int)((int64_t)(b + 1) * ell_sym / k);
     L.lo[b] = lo;
     L.width[b] = hi - lo;
     for (int c = lo; c < hi; ++c) L.mask[b][c >> 6] |= 1ull << (c & 63);
@@ -229,9 +230,11 @@ static std::vector<MaskDesc> make_masks(const BlockLayout& L, int d) {
   return out;
 }
 
-static int check_geometry(int64_t n, int ell, int k, int d) {
+// ell: symbols of sw bits (sw = 1: sign bits).
+static int check_geometry(int64_t n, int ell, int k, int d, int sw = 1) {
   if (n < 2 || n >= (1ll << 31)) return set_error("n must be in [2, 2^31)"), MSM_E_INVAL;
-  if (ell < 1 || ell > 256) return set_error("ell must be in [1, 256]"), MSM_E_INVAL;
+  if (sw != 1 && sw != 2 && sw != 4) return set_error("symbol bits must be 1, 2 or 4"), MSM_E_INVAL;
+  if (ell < 1 || ell * sw > 256) return set_error("ell * symbol bits must be in [1, 256]"), MSM_E_INVAL;
   if (k < 1 || k > ell || k > kMaxBlocks) return set_error("k must be in [1, min(ell, 32)]"), MSM_E_INVAL;
   if (d < 0 || d >= k) return set_error("d must be in [0, k)"), MSM_E_INVAL;
   double masks = 1.0;
@@ -356,7 +359,7 @@ static Tuning tuning_of(const msm_params* p) {
   return t;
 }
 
-static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
+static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int sw,
                    int k, int d, int Q, const Tuning& tu, int64_t cap0,
                    uint64_t** cand_out, int64_t* count_out, msm_stats* st,
                    PhaseTimer& tm, const SetTable& sets = SetTable(),
@@ -365,7 +368,7 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
   cudaStream_t s = sc.stream();
   const bool fused = fz.X != nullptr;
   int64_t total_cand = 0;
-  const BlockLayout L = make_layout(ell, k);
+  const BlockLayout L = make_layout(ell, k, sw);
   std::vector<MaskDesc> masks = make_masks(L, d);
   const int M = (int)masks.size();
   int maxkept = 0, maxwidth = 0, anygap = 0;
@@ -428,12 +431,12 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
   unsigned long long* checks_dev = counters + 1;
 
   // Field layout of every pool for the in-group checks, when the blocks fit.
-  const int FP = field_words(ell, k);
+  const int FP = field_words(ell, k, sw);
   uint32_t* fields = nullptr;
   if (FP > 0) {
     fields = (uint32_t*)sc.get(4 * (size_t)Q * n * FP);
     if (!fields) return MSM_E_NOMEM;
-    int rc = launch_fields(strings, (int64_t)Q * n, ell, k, fields, s);
+    int rc = launch_fields(strings, (int64_t)Q * n, ell, k, sw, fields, s);
     if (rc) return rc;
   }
 
@@ -478,6 +481,7 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
       pb.fields = fields;
       pb.FP = FP;
       pb.FU = (k + 1) / 2;
+      pb.sw = sw;
       pb.start_bits = sets.start_bits;
       pb.X = fz.X;
       pb.dtype = fz.dtype;
@@ -542,6 +546,10 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell,
     int rc = read_back(&ch, checks_dev, s);
     if (rc) return rc;
     st->Q = Q;
+    st->ell = ell;
+    st->k = k;
+    st->d = d;
+    st->S_est = -1.0;
     st->masks = (int64_t)Q * M;
     st->checks = (int64_t)ch;
     st->cand = total_cand;
@@ -622,6 +630,31 @@ static int run_projection(Scratch& sc, const void* X, int dtype, int64_t n,
   return rc;
 }
 
+// Output-size estimate of Sec. 4.3: the fraction of `samples` uniformly
+// random pairs within eps, times n(n - 1) / 2.
+static int estimate_output(Scratch& sc, const void* Xd, int dtype, int64_t n, int dim,
+                           int metric, float eps, const float* n32, int64_t samples,
+                           uint64_t seed, double* S) {
+  cudaStream_t s = sc.stream();
+  uint64_t* pr = (uint64_t*)sc.get(8 * (size_t)samples);
+  unsigned long long* cnt = (unsigned long long*)sc.get(256);
+  if (!pr || !cnt) return MSM_E_NOMEM;
+  MSM_CUDA(cudaMemsetAsync(cnt, 0, 256, s));
+  int rc = launch_random_pairs(seed, samples, n, pr, s);
+  if (rc) return rc;
+  rc = launch_recheck(Xd, dtype, n, dim, metric, eps, n32, pr, nullptr, samples, nullptr,
+                      nullptr, cnt, cnt + 1, s);
+  if (rc) return rc;
+  unsigned long long c = 0;
+  rc = read_back(&c, cnt, s);
+  if (rc) return rc;
+  sc.put(pr);
+  *S = (double)c / (double)samples * 0.5 * (double)n * (double)(n - 1);
+  return MSM_OK;
+}
+
+constexpr int64_t kAutoSamples = 1 << 22;
+
 static int bits_for(int64_t v) {
   int b = 0;
   while (b < 63 && ((int64_t)1 << b) <= v) ++b;
@@ -696,6 +729,98 @@ int msm_solve_Q(int ell, int d, double p, double gamma, int* Q) {
   return set_error("no Q <= 2^24 meets the bound"), MSM_E_INVAL;
 }
 
+// Sec. 4.3 parameter rule.  The string length is twice the bits needed to
+// index n points (so k - d blocks can hold log2 n letters), halved when the
+// estimated output is ~0; the replicate budget is max(30 S / n, 5) but below
+// 25; d is the smallest mismatch count whose bound-minimal Q fits the
+// budget, and k = 2d the fewest blocks for which k - d blocks hold half of
+// the string.
+int msm_choose_params(int64_t n, double p, double gamma, double S, int* ell, int* k, int* d,
+                      int* Q) {
+  if (n < 2 || !(p >= 0.0 && p < 1.0) || !(gamma > 0.0) || !(S >= 0.0) || !ell || !k || !d ||
+      !Q)
+    return set_error("invalid arguments to msm_choose_params"), MSM_E_INVAL;
+  int lg = 0;
+  while (lg < 62 && ((int64_t)1 << lg) < n) ++lg;  // ceil(log2 n)
+  int L = 2 * lg;
+  if (S < 1.0) L /= 2;
+  if (L < 1) L = 1;
+  if (L > 256) L = 256;
+  double budget = std::ceil(30.0 * S / (double)n);
+  if (budget < 5.0) budget = 5.0;
+  const int qmax = budget < 24.0 ? (int)budget : 24;
+  for (int dd = 0;; ++dd) {
+    const int kk = dd > 0 ? 2 * dd : 1;
+    if (kk > L || kk > kMaxBlocks)
+      return set_error("no mismatch count d meets the replicate budget"), MSM_E_INVAL;
+    int q = 0;
+    if (msm_solve_Q(L, dd, p, gamma, &q) == MSM_OK && q <= qmax) {
+      *ell = L;
+      *k = kk;
+      *d = dd;
+      *Q = q;
+      return MSM_OK;
+    }
+  }
+}
+
+int msm_estimate_output(const void* X, int64_t n, int dim, int dtype, int metric, float eps,
+                        int64_t samples, uint64_t seed, double* S, void* stream) {
+  if (!X || !S || n < 2 || n >= (1ll << 31) || dim < 1 || dim > kMaxDim || samples < 1 ||
+      !(eps >= 0.f) || (metric != MSM_COSINE && metric != MSM_EUCLIDEAN) ||
+      (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16) || !is_device_ptr(X))
+    return set_error("invalid msm_estimate_output arguments"), MSM_E_INVAL;
+  Scratch sc(nullptr, (cudaStream_t)stream);
+  double* n64;
+  float* n32;
+  int rc = norms_and_check(sc, X, dtype, n, dim, metric, &n64, &n32);
+  if (rc) return rc;
+  return estimate_output(sc, X, dtype, n, dim, metric, eps, n32, samples, seed, S);
+}
+
+double msm_e2lsh_p(double w) {
+  if (!(w > 0.0)) return -1.0;
+  const double phi_neg = 0.5 * std::erfc(w / std::sqrt(2.0));
+  const double coll = 1.0 - 2.0 * phi_neg -
+                      2.0 / (std::sqrt(2.0 * 3.14159265358979323846) * w) *
+                          (1.0 - std::exp(-0.5 * w * w));
+  return 1.0 - coll;
+}
+
+int msm_e2lsh_offsets(uint64_t seed, int64_t count, float* out, void* stream) {
+  if (count < 0 || (count > 0 && !out)) return set_error("bad offsets arguments"), MSM_E_INVAL;
+  return launch_e2lsh_offsets(seed, count, out, (cudaStream_t)stream);
+}
+
+int msm_project_e2lsh(const void* X, int64_t n, int dim, int dtype, const float* R,
+                      const float* u, float width, int ell, int Q, int symbol_bits,
+                      uint64_t* strings, int64_t* recomputed, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!X || !R || !u || !strings || n < 1 || n >= (1ll << 31) || dim < 1 || dim > kMaxDim ||
+      ell < 1 || Q < 1 || !(width > 0.f) ||
+      (symbol_bits != 1 && symbol_bits != 2 && symbol_bits != 4) || ell * symbol_bits > 256 ||
+      (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16))
+    return set_error("invalid msm_project_e2lsh arguments"), MSM_E_INVAL;
+  Scratch sc(nullptr, s);
+  float* xn = (float*)sc.get(4 * (size_t)n);
+  float* rn = (float*)sc.get(4 * (size_t)Q * ell);
+  unsigned* fl = (unsigned*)sc.get(256);
+  unsigned long long* re = (unsigned long long*)(fl ? (char*)fl + 64 : nullptr);
+  if (!xn || !rn || !fl) return MSM_E_NOMEM;
+  MSM_CUDA(cudaMemsetAsync(fl, 0, 256, s));
+  int rc = launch_row_norms(X, dtype, n, dim, nullptr, xn, fl, s);
+  if (!rc) rc = launch_col_norms(R, Q, dim, ell, rn, s);
+  if (!rc)
+    rc = launch_project_e2lsh(X, dtype, n, dim, R, rn, xn, u, Q, ell, symbol_bits, width,
+                              strings, re, s);
+  if (rc) return rc;
+  unsigned long long v = 0;
+  rc = read_back(&v, re, s);
+  if (rc) return rc;
+  if (recomputed) *recomputed = (int64_t)v;
+  return MSM_OK;
+}
+
 int msm_gaussian(uint64_t seed, int64_t count, float* out, void* stream) {
   if (count < 0 || (count > 0 && !out)) return set_error("bad gaussian arguments"), MSM_E_INVAL;
   return launch_gaussian(seed, count, out, (cudaStream_t)stream);
@@ -734,10 +859,11 @@ int msm_project(const void* X, int64_t n, int dim, int dtype, const float* R,
 }
 
 static int enumerate_impl(const uint64_t* strings, int64_t n, const int64_t* off, int S,
-                          int ell, int k, int d, int Q, int flags, const msm_allocator* alloc,
-                          msm_pairs* out, msm_stats* stats, cudaStream_t s) {
+                          int ell, int sw, int k, int d, int Q, int flags,
+                          const msm_allocator* alloc, msm_pairs* out, msm_stats* stats,
+                          cudaStream_t s) {
   if (!strings || !out || Q < 1) return set_error("invalid msm_enumerate arguments"), MSM_E_INVAL;
-  int rc = check_geometry(n, ell, k, d);
+  int rc = check_geometry(n, ell, k, d, sw);
   if (rc) return rc;
   out->pairs = nullptr;
   out->dist = nullptr;
@@ -752,7 +878,7 @@ static int enumerate_impl(const uint64_t* strings, int64_t n, const int64_t* off
   tm.mark(2);
   uint64_t* cand = nullptr;
   int64_t m = 0;
-  rc = run_msm(sc, strings, n, ell, k, d, Q, Tuning(), 0, &cand, &m, stats, tm, sets);
+  rc = run_msm(sc, strings, n, ell, sw, k, d, Q, Tuning(), 0, &cand, &m, stats, tm, sets);
   if (rc) return rc;
   if ((flags & MSM_FLAG_CANONICAL) && m > 1) {
     tm.mark(6);
@@ -776,8 +902,15 @@ static int enumerate_impl(const uint64_t* strings, int64_t n, const int64_t* off
 int msm_enumerate(const uint64_t* strings, int64_t n, int ell, int k, int d,
                   int Q, int flags, const msm_allocator* alloc,
                   msm_pairs* out, msm_stats* stats, void* stream) {
-  return enumerate_impl(strings, n, nullptr, 1, ell, k, d, Q, flags, alloc, out, stats,
+  return enumerate_impl(strings, n, nullptr, 1, ell, 1, k, d, Q, flags, alloc, out, stats,
                         (cudaStream_t)stream);
+}
+
+int msm_enumerate_symbols(const uint64_t* strings, int64_t n, int ell, int symbol_bits,
+                          int k, int d, int Q, int flags, const msm_allocator* alloc,
+                          msm_pairs* out, msm_stats* stats, void* stream) {
+  return enumerate_impl(strings, n, nullptr, 1, ell, symbol_bits, k, d, Q, flags, alloc, out,
+                        stats, (cudaStream_t)stream);
 }
 
 int msm_enumerate_sets(const uint64_t* strings, const int64_t* set_offsets, int nsets,
@@ -787,8 +920,8 @@ int msm_enumerate_sets(const uint64_t* strings, const int64_t* set_offsets, int 
   int64_t n = 0;
   int rc = check_sets(set_offsets, nsets, &n);
   if (rc) return rc;
-  return enumerate_impl(strings, n, set_offsets, nsets, ell, k, d, Q, flags, alloc, out, stats,
-                        (cudaStream_t)stream);
+  return enumerate_impl(strings, n, set_offsets, nsets, ell, 1, k, d, Q, flags, alloc, out,
+                        stats, (cudaStream_t)stream);
 }
 
 int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
@@ -820,6 +953,7 @@ int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
   return MSM_OK;
 }
 
+
 // A plan run of the count-only pipeline: the Scratch (recording or
 // replaying) and the device words the plan reads once the work is done.
 struct PlanCtx {
@@ -847,14 +981,27 @@ static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, i
       (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16) ||
       params->out_mode < 0 || params->out_mode > 2)
     return set_error("invalid msm_eps_graph arguments"), MSM_E_INVAL;
-  const int ell = params->ell, k = params->k, d = params->d;
-  int rc = check_geometry(n, ell, k, d);
+  // params->ell == 0: automatic parameters (Sec. 4.3), chosen once the row
+  // norms exist for the output-size estimate
+  const bool autop = params->ell == 0;
+  // String family: sign bits (Eq. 3) or E2LSH symbols of sw bits.  E2LSH
+  // buckets are measured against the Euclidean radius (eps, or sqrt(2 eps)
+  // for the cosine distance of unit rows).
+  const bool e2 = params->hash == MSM_HASH_E2LSH;
+  if (params->hash != MSM_HASH_SIGN && !e2) return set_error("unknown string family"), MSM_E_INVAL;
+  if (e2 && (params->Y || params->width < 0.f))
+    return set_error("E2LSH needs width >= 0 and no feature input"), MSM_E_INVAL;
+  const int sw = e2 ? (params->symbol_bits ? params->symbol_bits : 4) : 1;
+  const double radius = metric == MSM_EUCLIDEAN ? (double)eps : std::sqrt(2.0 * (double)eps);
+  float width = params->width > 0.f ? params->width : (float)(4.0 * radius);
+  int ell = params->ell, k = params->k, d = params->d;
+  int rc = autop ? (int)MSM_OK : check_geometry(n, ell, k, d, sw);
   if (rc) return rc;
+  double pcol = e2 ? msm_e2lsh_p((double)width / radius) : msm_collision_p(metric, eps);
+  if (pcol < 0.0) return set_error("invalid eps"), MSM_E_INVAL;
   int Q = params->Q;
-  if (Q <= 0) {
-    double p = msm_collision_p(metric, eps);
-    if (p < 0.0) return set_error("invalid eps"), MSM_E_INVAL;
-    rc = msm_solve_Q(ell, d, p, miss_ratio, &Q);
+  if (!autop && Q <= 0) {
+    rc = msm_solve_Q(ell, d, pcol, miss_ratio, &Q);
     if (rc) return rc;
   }
   out->pairs = nullptr;
@@ -892,6 +1039,28 @@ static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, i
   rc = norms_and_check(sc, Xd, dtype, n, dim, metric, &n64, &n32,
                        pc ? &pc->norm_flags : nullptr);
   if (rc) return rc;
+  double S_est = -1.0;
+  if (autop) {
+    if (pc) return set_error("plans need explicit string geometry"), MSM_E_INVAL;
+    rc = estimate_output(sc, Xd, dtype, n, dim, metric, eps, n32, kAutoSamples,
+                         params->seed ^ 0x5DEECE66Dull, &S_est);
+    if (rc) return rc;
+    if (e2 && !(params->width > 0.f)) {
+      // Sec. 4.3: w = 3.5 - log(S / 10 n) / 4 radii, clamped to [3.5, 12]
+      double w = 3.5 - std::log(S_est / (10.0 * (double)n) + 1e-300) / 4.0;
+      w = w < 3.5 ? 3.5 : (w > 12.0 ? 12.0 : w);
+      width = (float)(w * radius);
+      pcol = msm_e2lsh_p((double)width / radius);
+    }
+    int q = 0;
+    rc = msm_choose_params(n, pcol, miss_ratio, S_est, &ell, &k, &d, &q);
+    if (rc) return rc;
+    Q = params->Q > 0 ? params->Q : q;
+    if (e2 && ell * sw > 256) ell = 256 / sw;
+    if (k > ell) k = ell;
+    rc = check_geometry(n, ell, k, d, sw);
+    if (rc) return rc;
+  }
   // Projection input: X itself, or the learned features Y.
   const void* P = Xd;
   int pdim = dim, pdtype = dtype;
@@ -917,14 +1086,25 @@ static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, i
     if (rc) return rc;
     R = g;
   }
-  const int W = (ell + 63) / 64;
+  const int W = (ell * sw + 63) / 64;
   uint64_t* strings = (uint64_t*)sc.get(8 * (size_t)Q * n * W);
   unsigned long long* ctr = (unsigned long long*)sc.get(256);
   if (!strings || !ctr) return MSM_E_NOMEM;
   MSM_CUDA(cudaMemsetAsync(ctr, 0, 256, s));
   tm.mark(1);
-  rc = run_projection(sc, P, pdtype, n, pdim, R, pnorm, Q, ell, params->flags,
-                      strings, ctr + 2, pc ? &pc->proj_status : nullptr);
+  if (e2) {
+    float* u = (float*)sc.get(4 * (size_t)Q * ell);
+    float* rn = (float*)sc.get(4 * (size_t)Q * ell);
+    if (!u || !rn) return MSM_E_NOMEM;
+    rc = launch_e2lsh_offsets(params->seed, (int64_t)Q * ell, u, s);
+    if (!rc) rc = launch_col_norms(R, Q, pdim, ell, rn, s);
+    if (!rc)
+      rc = launch_project_e2lsh(P, pdtype, n, pdim, R, rn, pnorm, u, Q, ell, sw, width, strings,
+                                ctr + 2, s);
+  } else {
+    rc = run_projection(sc, P, pdtype, n, pdim, R, pnorm, Q, ell, params->flags,
+                        strings, ctr + 2, pc ? &pc->proj_status : nullptr);
+  }
   if (rc) return rc;
 
   uint64_t* cand = nullptr;
@@ -943,7 +1123,7 @@ static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, i
     fz.kept = ctr;
     fz.set_kept = set_kept;
   }
-  rc = run_msm(sc, strings, n, ell, k, d, Q, tuning_of(params),
+  rc = run_msm(sc, strings, n, ell, sw, k, d, Q, tuning_of(params),
                params->cand_capacity, &cand, &m, stats, tm, sets, fz,
                pc ? &pc->counters : nullptr);
   if (rc) return rc;
@@ -999,6 +1179,10 @@ static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, i
     stats->type1 = stats->cand - kept;
     stats->dist_recompute = (int64_t)h[1];
     stats->proj_recompute = (int64_t)h[2];
+    stats->ell = ell;
+    stats->k = k;
+    stats->d = d;
+    stats->S_est = S_est;
   }
   if (pairs) sc.release(pairs);
   if (dist) sc.release(dist);

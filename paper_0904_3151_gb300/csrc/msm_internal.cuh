@@ -12,16 +12,18 @@ constexpr int kMaxWords = 4;    // ell <= 256
 constexpr int kMaxBlocks = 32;  // k <= 32 (block sets fit a uint32 mask)
 constexpr int kMaxDim = 4096;
 
-// Bit layout of the k blocks of an ell-bit string (Sec. 2.2: blocks of
-// approximately equal length).  Passed to kernels by value.
+// Bit layout of the k blocks of a string of ell symbols of sw bits (sw = 1:
+// the sign bits of Eq. 3; sw = 2 or 4: E2LSH symbols), Sec. 2.2: blocks of
+// approximately equal length, aligned to symbols.  Passed to kernels by value.
 struct BlockLayout {
-  int ell, k, W;
+  int ell, k, W;  // ell: bits (symbols * sw)
+  int sw;         // bits per symbol
   int lo[kMaxBlocks];
   int width[kMaxBlocks];
   uint64_t mask[kMaxBlocks][kMaxWords];
 };
 
-BlockLayout make_layout(int ell, int k);
+BlockLayout make_layout(int ell_sym, int k, int sw = 1);
 
 // One grouping (replicate q, kept block set K) of the multiple sorting
 // method; the grouping key of a string is its K blocks.
@@ -119,6 +121,10 @@ void raw_free(const msm_allocator* a, void* p, cudaStream_t s);
 // ------------------------------------------------------ kernel launchers
 // rng.cu
 int launch_gaussian(uint64_t seed, int64_t count, float* out, cudaStream_t s);
+// E2LSH bucket offsets in [0, 1) (Philox4x64-10, key {seed, 2}).
+int launch_e2lsh_offsets(uint64_t seed, int64_t count, float* out, cudaStream_t s);
+// m uniform random pairs i != j of n points (Philox4x64-10, key {seed, 1}).
+int launch_random_pairs(uint64_t seed, int64_t m, int64_t n, uint64_t* out, cudaStream_t s);
 
 // project.cu
 // Row norms in double (sequential fma of squares, then sqrt) plus a flag
@@ -128,6 +134,12 @@ int launch_row_norms(const void* X, int dtype, int64_t n, int dim,
                      cudaStream_t s);
 int launch_col_norms(const float* R, int Q, int dim, int ell, float* rn,
                      cudaStream_t s);
+// E2LSH symbols: low sw bits of floor(r^T x / width + u), strings
+// [Q][n][ceil(ell sw / 64)]; rnorm: column norms of R, xnorm: row norms.
+int launch_project_e2lsh(const void* X, int dtype, int64_t n, int dim, const float* R,
+                         const float* rnorm, const float* xnorm, const float* u, int Q,
+                         int ell, int sw, float width, uint64_t* strings,
+                         unsigned long long* recompute, cudaStream_t s);
 int launch_project(const void* X, int dtype, int64_t n, int dim,
                    const float* R, const float* rnorm, const float* xnorm,
                    int Q, int ell, uint64_t* strings,
@@ -226,6 +238,7 @@ struct PairBatch {
   unsigned long long* set_kept = nullptr;  // per-set pairs within eps (or NULL)
   const int64_t* set_off = nullptr;      // device [nsets + 1]
   int nsets = 1;
+  int sw = 1;                            // bits per symbol (1: sign bits)
   // launch tuning of the pair check (0 = defaults)
   int ctas_per_sm = 0;
   int min_blocks = 0;                    // fused variant: 2, 4 or 5
@@ -233,8 +246,8 @@ struct PairBatch {
 size_t pairs_scratch_bytes(int64_t items);
 // Field layout: every block in its own 16-bit field, FP (even) words per
 // string; field_words returns 0 when a block exceeds 15 bits or k > 16.
-int field_words(int ell, int k);
-int launch_fields(const uint64_t* strings, int64_t count, int ell, int k,
+int field_words(int ell_sym, int k, int sw = 1);
+int launch_fields(const uint64_t* strings, int64_t count, int ell_sym, int k, int sw,
                   uint32_t* fields, cudaStream_t s);
 // Finds the groups of >= 2 equal keys; returns on the device the number
 // of work items and adds sum C(size,2) to *checks_dev.

@@ -274,7 +274,21 @@ struct CheckArgs {
   unsigned long long* set_kept;
   const int64_t* set_off;
   int nsets;
+  int sw;  // bits per symbol: Hamming distances count differing symbols
 };
+
+// Number of differing symbols in x = a ^ b (symbols of sw = 1, 2 or 4 bits
+// start at multiples of sw within every 16-bit field and every word).
+__device__ __forceinline__ uint32_t sym_diff32(uint32_t x, int sw) {
+  if (sw == 2) return (x | (x >> 1)) & 0x55555555u;
+  if (sw == 4) return (x | (x >> 1) | (x >> 2) | (x >> 3)) & 0x11111111u;
+  return x;
+}
+__device__ __forceinline__ uint64_t sym_diff64(uint64_t x, int sw) {
+  if (sw == 2) return (x | (x >> 1)) & 0x5555555555555555ull;
+  if (sw == 4) return (x | (x >> 1) | (x >> 2) | (x >> 3)) & 0x1111111111111111ull;
+  return x;
+}
 
 // ------------------------------------------------------- fused recheck
 // In count-only mode the pairs that pass the tests of a work item are not
@@ -434,7 +448,7 @@ __device__ __forceinline__ bool strings_ok(const CheckArgs& a,
   }
   int h = 0;
 #pragma unroll
-  for (int w = 0; w < W; ++w) h += __popcll(x[w]);
+  for (int w = 0; w < W; ++w) h += __popcll(sym_diff64(x[w], a.sw));
   if (h > a.d) return false;
   if (hashed) {
     uint64_t o = 0;
@@ -453,7 +467,7 @@ __device__ __forceinline__ bool replicates_ok(const CheckArgs& a, uint32_t i,
     const uint64_t* gj = a.strings + ((size_t)g * a.n + j) * W;
     int hg = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) hg += __popcll(__ldg(gi + w) ^ __ldg(gj + w));
+    for (int w = 0; w < W; ++w) hg += __popcll(sym_diff64(__ldg(gi + w) ^ __ldg(gj + w), a.sw));
     if (hg <= a.d) return false;
   }
   return true;
@@ -717,10 +731,11 @@ __device__ __forceinline__ bool gaps_differ(const uint32_t (&fa)[FP],
   return bad == 0;
 }
 
-// Hamming <= d and (hashed keys only) all kept fields equal.
+// Hamming (differing symbols) <= d and (hashed keys only) all kept fields
+// equal.
 template <int FP, int FU>
 __device__ __forceinline__ bool fields_rest_ok(const uint32_t (&fa)[FP],
-                                               const uint32_t* fb, int d,
+                                               const uint32_t* fb, int d, int sw,
                                                bool hashed,
                                                const uint32_t (&keepf)[FP]) {
   int h = 0;
@@ -728,7 +743,7 @@ __device__ __forceinline__ bool fields_rest_ok(const uint32_t (&fa)[FP],
 #pragma unroll
   for (int w = 0; w < FU; ++w) {
     const uint32_t x = fa[w] ^ fb[w];
-    h += __popc(x);
+    h += __popc(sym_diff32(x, sw));
     bad |= keepf[w] & ((x + 0x7FFF7FFFu) & 0x80008000u);
   }
   return h <= d && (!hashed || bad == 0);
@@ -745,7 +760,7 @@ __device__ __forceinline__ bool replicates_ok_fields(const CheckArgs& a,
 #pragma unroll
     for (int w = 0; w < FP / 2; ++w) {
       const uint2 p = __ldg(fi + w), q2 = __ldg(fj + w);
-      h += __popc(p.x ^ q2.x) + __popc(p.y ^ q2.y);
+      h += __popc(sym_diff32(p.x ^ q2.x, a.sw)) + __popc(sym_diff32(p.y ^ q2.y, a.sw));
     }
     if (h <= a.d) return false;
   }
@@ -843,7 +858,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
 #pragma unroll
           for (int w = 0; w < FP; ++w) fa[w] = sm_f[warp][aa][w];
           if (gaps_differ<FP, FU>(fa, sm_f[warp][b], gapf) &&
-              fields_rest_ok<FP, FU>(fa, sm_f[warp][b], a.d, hashed, keepf)) {
+              fields_rest_ok<FP, FU>(fa, sm_f[warp][b], a.d, a.sw, hashed, keepf)) {
             ii = sm_i[warp][aa];
             jj = sm_i[warp][b];
             pass = replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj, ii < jj ? jj : ii);
@@ -957,7 +972,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
             uint32_t fr[FP];
 #pragma unroll
             for (int w = 0; w < FP; ++w) fr[w] = sm_fr[warp][r][w];
-            if (fields_rest_ok<FP, FU>(fr, sm_f[warp][c], a.d, hashed, keepf)) {
+            if (fields_rest_ok<FP, FU>(fr, sm_f[warp][c], a.d, a.sw, hashed, keepf)) {
               ii = sm_ir[warp][r];
               jj = sm_i[warp][c];
               ok = replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj, ii < jj ? jj : ii);
@@ -1016,25 +1031,26 @@ int launch_set_counts(const uint64_t* pairs, int64_t m, const int64_t* off, int 
 
 // Field layout of the strings: usable when every block fits 15 bits and the
 // blocks fit 8 words.  Returns the padded word count FP (even), or 0.
-int field_words(int ell, int k) {
+int field_words(int ell_sym, int k, int sw) {
   if (k > kMaxFieldBlocks) return 0;
   for (int b = 0; b < k; ++b) {
-    const int w = (int)((int64_t)(b + 1) * ell / k - (int64_t)b * ell / k);
+    const int w = sw * (int)((int64_t)(b + 1) * ell_sym / k - (int64_t)b * ell_sym / k);
     if (w > 15) return 0;
   }
   const int F = (k + 1) / 2;
   return (F + 1) & ~1;
 }
 
-int launch_fields(const uint64_t* strings, int64_t count, int ell, int k,
+int launch_fields(const uint64_t* strings, int64_t count, int ell_sym, int k, int sw,
                   uint32_t* fields, cudaStream_t s) {
-  const int FP = field_words(ell, k);
+  const int FP = field_words(ell_sym, k, sw);
+  const int ell = ell_sym * sw;
   const int W = (ell + 63) / 64;
   FieldLayout L;
   L.k = k;
   for (int b = 0; b < kMaxFieldBlocks; ++b) {
-    L.lo[b] = b < k ? (int)((int64_t)b * ell / k) : 0;
-    L.width[b] = b < k ? (int)((int64_t)(b + 1) * ell / k) - L.lo[b] : 0;
+    L.lo[b] = b < k ? sw * (int)((int64_t)b * ell_sym / k) : 0;
+    L.width[b] = b < k ? sw * (int)((int64_t)(b + 1) * ell_sym / k) - L.lo[b] : 0;
   }
   int64_t grid = (count + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 16;
@@ -1138,6 +1154,7 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   a.set_kept = b.set_kept;
   a.set_off = b.set_off;
   a.nsets = b.nsets;
+  a.sw = b.sw > 0 ? b.sw : 1;
   const bool fuse = b.X != nullptr;
   if (fuse && !b.kept) return set_error("fused recheck needs counters"), MSM_E_INVAL;
   const int mb = b.min_blocks ? b.min_blocks : 4;

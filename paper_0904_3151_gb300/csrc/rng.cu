@@ -49,7 +49,56 @@ __global__ void gaussian_kernel(uint64_t seed, int64_t count, float* out) {
   }
 }
 
+// Uniform random pairs (i, j), i != j, of n points, stored (min << 32) |
+// max: pair t comes from block t of the same generator under key {seed, 1}
+// (words w0, w1); i = w0 mod n, j = w1 mod (n - 1), shifted past i.
+__global__ void random_pairs_kernel(uint64_t seed, int64_t m, int64_t n, uint64_t* out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const U64x4 w = philox4x64_10((uint64_t)t, 0, 0, 0, seed, 1);
+    const uint64_t i = w.v[0] % (uint64_t)n;
+    uint64_t j = w.v[1] % (uint64_t)(n - 1);
+    if (j >= i) ++j;
+    out[t] = i < j ? ((i << 32) | j) : ((j << 32) | i);
+  }
+}
+
+// E2LSH bucket offsets: element e is the top 24 bits of word 0 of block e
+// under key {seed, 2}, times 2^-24 (uniform on [0, 1), exact in float).
+__global__ void e2lsh_offsets_kernel(uint64_t seed, int64_t count, float* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const U64x4 w = philox4x64_10((uint64_t)e, 0, 0, 0, seed, 2);
+    out[e] = (float)((double)(w.v[0] >> 40) * 0x1.0p-24);
+  }
+}
+
 }  // namespace
+
+int launch_e2lsh_offsets(uint64_t seed, int64_t count, float* out, cudaStream_t s) {
+  if (count <= 0) return MSM_OK;
+  int64_t grid = (count + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (grid > cap) grid = cap;
+  kt_begin(KC_OTHER, s);
+  e2lsh_offsets_kernel<<<(int)grid, 256, 0, s>>>(seed, count, out);
+  kt_end(s);
+  MSM_LAUNCH("e2lsh_offsets_kernel");
+  return MSM_OK;
+}
+
+int launch_random_pairs(uint64_t seed, int64_t m, int64_t n, uint64_t* out, cudaStream_t s) {
+  if (m <= 0) return MSM_OK;
+  if (n < 2) return set_error("random pairs need n >= 2"), MSM_E_INVAL;
+  int64_t grid = (m + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (grid > cap) grid = cap;
+  kt_begin(KC_OTHER, s);
+  random_pairs_kernel<<<(int)grid, 256, 0, s>>>(seed, m, n, out);
+  kt_end(s);
+  MSM_LAUNCH("random_pairs_kernel");
+  return MSM_OK;
+}
 
 int launch_gaussian(uint64_t seed, int64_t count, float* out, cudaStream_t s) {
   if (count <= 0) return MSM_OK;

@@ -98,3 +98,9 @@ def test_choose_params_matches_oracle(L):
                         msm.choose_params(n, p, 1e-6, S)
                     continue
                 assert msm.choose_params(n, p, 1e-6, S) == want, (n, eps, S)
+
+
+def test_e2lsh_probability_matches_oracle(L):
+    for w in (0.25, 1.0, 3.5, 7.0, 12.0):
+        assert L.msm_e2lsh_p(w) == pytest.approx(oracle.e2lsh_p(w), rel=1e-13, abs=1e-15)
+    assert L.msm_e2lsh_p(0.0) == -1.0
