@@ -300,6 +300,43 @@ def run_lsh_d0(msm, X, wl, n, truth, steps, stream, Q=300, gamma=1e-6):
                     "for gamma = 1e-6 at the radius"}
 
 
+def run_e2lsh(msm, X, wl, n, ms_plain, stream, steps=2):
+    """E2LSH symbol strings (Datar et al.; Sec. 3.1 and the width rule of
+    Sec. 4.3) on the scale data read as Euclidean: on unit rows cosine 0.1
+    is Euclidean sqrt(0.2).  32 symbols of 2 bits, k = 8, d = 4 (70
+    groupings), bucket width 4 radii; Q is the smallest whose measured
+    missing ratio is <= 1e-6 (counts through the fused count-only path)."""
+    eps = float(np.sqrt(np.float32(2.0 * wl.eps)))
+    truth = msm.eps_count_exhaustive(X, msm.EUCLIDEAN, eps)
+    ell, k, d, sw = 32, 8, 4, 2
+    e2 = {"symbol_bits": sw, "width": float(np.float32(4.0 * eps))}
+    ladder, Q = [], None
+    for q in range(2, 17):
+        _, _, st = msm.eps_graph(X, msm.EUCLIDEAN, eps, ell, k, d, Q=q, seed=wl.r_seed + 21,
+                                 out_mode=msm.OUT_COUNT, e2lsh=e2)
+        r = (truth - st["count"]) / max(1, truth)
+        ladder.append({"Q": q, "missing_ratio": r})
+        if r <= 1e-6:
+            Q = q
+            break
+    if Q is None:
+        return {"Q_ladder": ladder, "note": "no Q <= 16 reached 1e-6"}
+
+    def step():
+        return msm.eps_graph(X, msm.EUCLIDEAN, eps, ell, k, d, Q=Q, seed=wl.r_seed + 21,
+                             out_mode=msm.OUT_PAIRS, cand_capacity=600 * n, e2lsh=e2)
+    step()
+    ms, (pr, _, st) = time_steps(step, steps, stream)
+    del pr
+    return {"value": n / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms, "Q": Q, "ell": ell,
+            "symbol_bits": sw, "k": k, "d": d, "width_radii": 4.0, "eps_euclidean": eps,
+            "missing_ratio": (truth - st["count"]) / max(1, truth), "pairs": st["count"],
+            "checks": st["checks"], "speedup_vs_plain": ms_plain / ms, "Q_ladder": ladder,
+            "kernel_ms": st["kernel_ms"],
+            "note": "E2LSH symbol strings through the same grouping and pair-check kernels; "
+                    "plain = sign strings on the same points (cosine 0.1)"}
+
+
 def run_auto_params(msm, X, wl, n, truth, steps, stream, gamma=1e-6):
     """Automatic parameters (Sec. 4.3): l, k, d and Q from the paper's rule
     applied to a sampled output-size estimate, on the scale workload."""
@@ -656,8 +693,9 @@ def main():
             forms["batched"] = run_batched(msm, max(2, min(3, a.steps)), stream)
         if not a.no_precision:
             forms["precision"] = run_precision(msm, 2, stream)
-        forms["lsh_d0"] = run_lsh_d0(msm, X, wl, n, missing["truth_pairs"], 2, stream)
+        forms["lsh_d0"] = run_lsh_d0(msm, X, wl, n, missing["truth_pairs"], 1, stream)
         forms["auto_params"] = run_auto_params(msm, X, wl, n, missing["truth_pairs"], 2, stream)
+        forms["e2lsh"] = run_e2lsh(msm, X, wl, n, ms, stream)
         forms["output_sensitivity"] = run_output_sensitivity(msm, wl, Q, stream)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
