@@ -534,6 +534,7 @@ def main():
     import torch
     import paper_0904_3151_gb300 as msm
     from paper_0904_3151_gb300 import build as b
+    from paper_0904_3151_gb300 import replicas
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -551,7 +552,7 @@ def main():
 
     n = a.n or wl.n
     # weak scaling: every rank owns an independent point set of the workload
-    Xh = W.clustered(n, wl.dim, wl.n_clusters, wl.sigma, wl.data_seed + 7919 * rank)
+    Xh = W.clustered(n, wl.dim, wl.n_clusters, wl.sigma, replicas.replica_seed(wl.data_seed, rank))
     X = torch.from_numpy(Xh).cuda()
     seed = wl.r_seed
     stream = torch.cuda.current_stream()
@@ -590,12 +591,8 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / a.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms / 1000.0)
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / a.steps, dist, "cuda")
+    value = replicas.job_throughput(world, n, ms)
     pairs_per_s = world * counts[-1] / (ms / 1000.0)
 
     # ---- e2e: host X in, host pairs out, through the same API
@@ -622,12 +619,8 @@ def main():
             del p, dv
         f1.record(stream)
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1) / reps
-        if dist:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * n / (ems / 1000.0), "unit": UNIT,
+        ems = replicas.max_over_ranks(f0.elapsed_time(f1) / reps, dist, "cuda")
+        e2e = {"value": replicas.job_throughput(world, n, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(Xh.nbytes), "d2h_bytes_per_step": int(bo),
                "ms_per_step": ems}
 
