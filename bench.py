@@ -302,17 +302,19 @@ def run_lsh_d0(msm, X, wl, n, truth, steps, stream, Q=300, gamma=1e-6):
 
 def run_e2lsh(msm, X, wl, n, ms_plain, stream, steps=2):
     """E2LSH symbol strings (Datar et al.; Sec. 3.1 and the width rule of
-    Sec. 4.3) on the scale data read as Euclidean: on unit rows cosine 0.1
-    is Euclidean sqrt(0.2).  32 symbols of 2 bits, k = 8, d = 4 (70
-    groupings), bucket width 4 radii; Q is the smallest whose measured
-    missing ratio is <= 1e-6 (counts through the fused count-only path)."""
-    eps = float(np.sqrt(np.float32(2.0 * wl.eps)))
-    truth = msm.eps_count_exhaustive(X, msm.EUCLIDEAN, eps)
+    Sec. 4.3) for the same problem as the plain form (cosine eps = 0.1 on the
+    unit rows of the scale workload; the buckets are measured against the
+    equivalent Euclidean radius sqrt(2 eps)).  32 symbols of 2 bits, k = 8,
+    d = 4 (70 groupings), bucket width 4 radii; Q is the smallest whose
+    measured missing ratio is <= 1e-6 (counts through the fused path)."""
+    eps = wl.eps
+    radius = float(np.sqrt(np.float32(2.0 * np.float32(eps))))
+    truth = msm.eps_count_exhaustive(X, msm.COSINE, eps)
     ell, k, d, sw = 32, 8, 4, 2
-    e2 = {"symbol_bits": sw, "width": float(np.float32(4.0 * eps))}
+    e2 = {"symbol_bits": sw, "width": float(np.float32(4.0 * radius))}
     ladder, Q = [], None
     for q in range(2, 17):
-        _, _, st = msm.eps_graph(X, msm.EUCLIDEAN, eps, ell, k, d, Q=q, seed=wl.r_seed + 21,
+        _, _, st = msm.eps_graph(X, msm.COSINE, eps, ell, k, d, Q=q, seed=wl.r_seed + 21,
                                  out_mode=msm.OUT_COUNT, e2lsh=e2)
         r = (truth - st["count"]) / max(1, truth)
         ladder.append({"Q": q, "missing_ratio": r})
@@ -323,18 +325,18 @@ def run_e2lsh(msm, X, wl, n, ms_plain, stream, steps=2):
         return {"Q_ladder": ladder, "note": "no Q <= 16 reached 1e-6"}
 
     def step():
-        return msm.eps_graph(X, msm.EUCLIDEAN, eps, ell, k, d, Q=Q, seed=wl.r_seed + 21,
+        return msm.eps_graph(X, msm.COSINE, eps, ell, k, d, Q=Q, seed=wl.r_seed + 21,
                              out_mode=msm.OUT_PAIRS, cand_capacity=600 * n, e2lsh=e2)
     step()
     ms, (pr, _, st) = time_steps(step, steps, stream)
     del pr
     return {"value": n / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms, "Q": Q, "ell": ell,
-            "symbol_bits": sw, "k": k, "d": d, "width_radii": 4.0, "eps_euclidean": eps,
+            "symbol_bits": sw, "k": k, "d": d, "width_radii": 4.0, "radius_euclidean": radius,
             "missing_ratio": (truth - st["count"]) / max(1, truth), "pairs": st["count"],
             "checks": st["checks"], "speedup_vs_plain": ms_plain / ms, "Q_ladder": ladder,
             "kernel_ms": st["kernel_ms"],
-            "note": "E2LSH symbol strings through the same grouping and pair-check kernels; "
-                    "plain = sign strings on the same points (cosine 0.1)"}
+            "note": "E2LSH symbol strings through the same grouping and pair-check kernels, "
+                    "same problem as the plain form (cosine 0.1 on unit rows)"}
 
 
 def run_auto_params(msm, X, wl, n, truth, steps, stream, gamma=1e-6):
@@ -442,9 +444,17 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
-def kernel_source_hash():
+# Sources that determine a kernel class's work and memory traffic: its own
+# kernels, the grouping that feeds them, and the shared headers.
+KERNEL_SOURCES = {
+    "pair_check": ["pairs.cu", "group.cu", "distance.cuh", "msm_internal.cuh"],
+}
+
+
+def kernel_source_hash(kind="pair_check"):
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_0904_3151_gb300", "csrc"))):
+    for f in sorted(KERNEL_SOURCES.get(kind, os.listdir(
+            os.path.join(ROOT, "paper_0904_3151_gb300", "csrc")))):
         h.update(open(os.path.join(ROOT, "paper_0904_3151_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -477,7 +487,7 @@ def traffic_for(kind, workload):
     except ValueError:
         return None
     e = d.get(kind)
-    if not e or e.get("source_hash") != kernel_source_hash() or e.get("workload") != workload:
+    if not e or e.get("source_hash") != kernel_source_hash(kind) or e.get("workload") != workload:
         return None
     return e.get("bytes_per_launch")
 

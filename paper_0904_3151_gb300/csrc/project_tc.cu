@@ -338,8 +338,11 @@ __device__ __forceinline__ float ldx(const void* X, int dtype, int64_t i) {
 
 // One warp per queued bit: float dot with its own bound, then the
 // double-precision sequential-fma value when still undecided.
+// Rt: optional transposed float copy of R (row q * W * 64 + c holds column c
+// of R_q, contiguous over the coordinates); the values are R's, only the
+// loads of a column become coalesced.
 __global__ void project_fix_kernel(const void* X, int dtype, int64_t n, int dim,
-                                   const float* R, int ell, int W,
+                                   const float* R, const float* Rt, int ell, int W,
                                    const float* xnorm, const float* rnorm_pad,
                                    const uint64_t* fix,
                                    const unsigned long long* fix_count,
@@ -362,8 +365,10 @@ __global__ void project_fix_kernel(const void* X, int dtype, int64_t n, int dim,
     const int qc = (int)(e & 0xffffffffu);
     const int q = qc / ell, c = qc % ell;
     const float* Rq = R + (size_t)q * dim * ell;
+    const float* rc = Rt ? Rt + (size_t)(q * W * 64 + c) * dim : nullptr;
     float acc = 0.f;
-    for (int k = lane; k < dim; k += 32) acc = fmaf(ldx(X, dtype, row * dim + k), Rq[(size_t)k * ell + c], acc);
+    for (int k = lane; k < dim; k += 32)
+      acc = fmaf(ldx(X, dtype, row * dim + k), rc ? rc[k] : Rq[(size_t)k * ell + c], acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
@@ -372,7 +377,8 @@ __global__ void project_fix_kernel(const void* X, int dtype, int64_t n, int dim,
       if (fabsf(acc) <= marg) {
         double t = 0.0;
         for (int k = 0; k < dim; ++k)
-          t = fma((double)ldx(X, dtype, row * dim + k), (double)Rq[(size_t)k * ell + c], t);
+          t = fma((double)ldx(X, dtype, row * dim + k),
+                  (double)(rc ? rc[k] : Rq[(size_t)k * ell + c]), t);
         bit = t > 0.0;
         atomicAdd(recompute, 1ull);
       } else {
@@ -513,9 +519,10 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
     // no host round trip: the fix-up reads the queue length on the device
     // and reports an overflow in *status (bit 1) for the caller to act on
     kt_begin(KC_PROJECT, s);
-    project_fix_kernel<<<num_sms() * 16, 256, 0, s>>>(X, dtype, n, dim, R, ell, W, xnorm, rnorm,
-                                                      fix, fix_count, fix_cap, strings,
-                                                      recompute, status);
+    project_fix_kernel<<<num_sms() * 16, 256, 0, s>>>(X, dtype, n, dim, R,
+                                                      bf16 ? nullptr : (const float*)Bhi, ell,
+                                                      W, xnorm, rnorm, fix, fix_count, fix_cap,
+                                                      strings, recompute, status);
     kt_end(s);
     MSM_LAUNCH("project_fix_kernel");
     return MSM_OK;
@@ -538,8 +545,10 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
     const int cap = num_sms() * 16;
     if (grid2 > cap) grid2 = cap;
     kt_begin(KC_PROJECT, s);
-    project_fix_kernel<<<grid2, 256, 0, s>>>(X, dtype, n, dim, R, ell, W, xnorm, rnorm, fix,
-                                              fix_count, fix_cap, strings, recompute, status);
+    project_fix_kernel<<<grid2, 256, 0, s>>>(X, dtype, n, dim, R,
+                                              bf16 ? nullptr : (const float*)Bhi, ell, W, xnorm,
+                                              rnorm, fix, fix_count, fix_cap, strings, recompute,
+                                              status);
     kt_end(s);
     MSM_LAUNCH("project_fix_kernel");
   }
