@@ -359,19 +359,24 @@ __global__ void project_fix_kernel(const void* X, int dtype, int64_t n, int dim,
     return;
   }
   const float m2 = (float)(2 * dim + 8) * 0x1.0p-24f;
-  for (int64_t it = warp; it < m; it += nwarps) {
-    const uint64_t e = fix[it];
+  // four queued signs per warp, eight lanes each (more loads in flight)
+  const int sub = lane & 7, grp = lane >> 3;
+  for (int64_t base = warp * 4; base < m; base += nwarps * 4) {
+    const int64_t it = base + grp;
+    const bool valid = it < m;
+    const uint64_t e = valid ? fix[it] : 0ull;
     const int64_t row = (int64_t)(e >> 32);
     const int qc = (int)(e & 0xffffffffu);
     const int q = qc / ell, c = qc % ell;
     const float* Rq = R + (size_t)q * dim * ell;
     const float* rc = Rt ? Rt + (size_t)(q * W * 64 + c) * dim : nullptr;
     float acc = 0.f;
-    for (int k = lane; k < dim; k += 32)
-      acc = fmaf(ldx(X, dtype, row * dim + k), rc ? rc[k] : Rq[(size_t)k * ell + c], acc);
+    if (valid)
+      for (int k = sub; k < dim; k += 8)
+        acc = fmaf(ldx(X, dtype, row * dim + k), rc ? rc[k] : Rq[(size_t)k * ell + c], acc);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
+    for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (valid && sub == 0) {
       bool bit;
       const float marg = m2 * xnorm[row] * rnorm_pad[q * W * 64 + c] + (float)dim * 0x1.0p-120f;
       if (fabsf(acc) <= marg) {
