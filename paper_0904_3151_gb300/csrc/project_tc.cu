@@ -24,10 +24,11 @@ namespace msm {
 namespace {
 
 constexpr int kRows = 128;      // M of the MMA, rows per CTA
-constexpr int kCols = 128;      // N of the MMA, columns per tile
+constexpr int kCols = 64;       // N of the MMA, columns per tile (one word)
 constexpr int kChunkBytes = 128;  // K bytes per swizzle atom row
 constexpr int kMaxChunks = 4;   // K chunks kept resident (D*esize <= 512 B)
-constexpr int kTileBytes = kRows * kChunkBytes;  // one 128 x 128 B box
+constexpr int kTileBytes = kRows * kChunkBytes;  // one 128 x 128 B box of X
+constexpr int kBTileBytes = kCols * kChunkBytes; // one 64 x 128 B box of R
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -155,7 +156,7 @@ struct TcArgs {
 // 128 threads: warp 0 also allocates TMEM; thread 0 issues TMA and MMA; all
 // four warps read TMEM (warp w owns lanes 32w..32w+31 = rows).
 template <bool BF16>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
 project_tc_kernel(const __grid_constant__ CUtensorMap tmX,
                   const __grid_constant__ CUtensorMap tmB,
                   const __grid_constant__ CUtensorMap tmB2, TcArgs a) {
@@ -163,8 +164,8 @@ project_tc_kernel(const __grid_constant__ CUtensorMap tmX,
   constexpr int kNB = BF16 ? 2 : 1;  // B operands (R high, R low)
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = base;
-  uint8_t* sB = base + kMaxChunks * kTileBytes;
-  uint64_t* bars = (uint64_t*)(sB + kNB * kMaxChunks * kTileBytes);
+  uint8_t* sB = base + a.chunks * kTileBytes;  // then kNB * chunks boxes of R
+  uint64_t* bars = (uint64_t*)(sB + kNB * a.chunks * kBTileBytes);
   uint32_t* tslot = (uint32_t*)(bars + 4);
   uint64_t* barA = bars;
   uint64_t* barB = bars + 1;
@@ -205,12 +206,12 @@ project_tc_kernel(const __grid_constant__ CUtensorMap tmX,
   for (int ct = 0; ct < a.ctiles && !failed; ++ct) {
     const uint32_t par = ct & 1;
     if (tid == 0) {
-      mbar_expect_tx(barB, (uint32_t)(kNB * a.chunks * kTileBytes));
+      mbar_expect_tx(barB, (uint32_t)(kNB * a.chunks * kBTileBytes));
       for (int c = 0; c < a.chunks; ++c) {
         const int kx = c * (kChunkBytes / (BF16 ? 2 : 4));
-        tma_load_2d(sB + c * kTileBytes, &tmB, barB, kx, ct * kCols);
+        tma_load_2d(sB + c * kBTileBytes, &tmB, barB, kx, ct * kCols);
         if (BF16)
-          tma_load_2d(sB + (kMaxChunks + c) * kTileBytes, &tmB2, barB, kx, ct * kCols);
+          tma_load_2d(sB + (a.chunks + c) * kBTileBytes, &tmB2, barB, kx, ct * kCols);
       }
       bool ok = (ct > 0 || mbar_wait(barA, 0, a.status)) && mbar_wait(barB, par, a.status);
       if (ok) {
@@ -219,11 +220,11 @@ project_tc_kernel(const __grid_constant__ CUtensorMap tmX,
         for (int c = 0; c < a.chunks; ++c)
           for (int ks = 0; ks < ksteps; ++ks) {
             const uint64_t ad = sw128_desc(saddr(sA + c * kTileBytes) + ks * 32);
-            const uint64_t bd = sw128_desc(saddr(sB + c * kTileBytes) + ks * 32);
+            const uint64_t bd = sw128_desc(saddr(sB + c * kBTileBytes) + ks * 32);
             mma<BF16>(tmem, ad, bd, a.idesc, acc);
             acc = 1;
             if (BF16) {
-              const uint64_t bd2 = sw128_desc(saddr(sB + (kMaxChunks + c) * kTileBytes) + ks * 32);
+              const uint64_t bd2 = sw128_desc(saddr(sB + (a.chunks + c) * kBTileBytes) + ks * 32);
               mma<BF16>(tmem, ad, bd2, a.idesc, 1);
             }
           }
@@ -418,13 +419,13 @@ EncodeFn get_encode() {
 
 // 2-D map over a row-major [rows][inner] matrix, box = 128 B x 128 rows.
 int make_map(CUtensorMap* m, const void* ptr, bool bf16, int64_t inner,
-             int64_t rows) {
+             int64_t rows, int box_rows) {
   EncodeFn enc = get_encode();
   if (!enc) return set_error("cuTensorMapEncodeTiled unavailable"), MSM_E_CUDA;
   const int es = bf16 ? 2 : 4;
   cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
   cuuint64_t gstride[1] = {(cuuint64_t)(inner * es)};
-  cuuint32_t box[2] = {(cuuint32_t)(kChunkBytes / es), (cuuint32_t)kRows};
+  cuuint32_t box[2] = {(cuuint32_t)(kChunkBytes / es), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                    2, const_cast<void*>(ptr), gdim, gstride, box, estr,
@@ -481,9 +482,9 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
     MSM_LAUNCH("transpose_R_kernel");
   }
   CUtensorMap mX, mB, mB2;
-  int rc = make_map(&mX, X, bf16, dim, n);
-  if (!rc) rc = make_map(&mB, Bhi, bf16, dim, rows);
-  if (!rc) rc = make_map(&mB2, bf16 ? Blo : Bhi, bf16, dim, rows);
+  int rc = make_map(&mX, X, bf16, dim, n, kRows);
+  if (!rc) rc = make_map(&mB, Bhi, bf16, dim, rows, kCols);
+  if (!rc) rc = make_map(&mB2, bf16 ? Blo : Bhi, bf16, dim, rows, kCols);
   if (rc) return rc;
 
   TcArgs a;
@@ -511,7 +512,10 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
   a.status = status;
 
   const int kNB = bf16 ? 2 : 1;
-  const size_t smem = 1024 + (size_t)(1 + kNB) * kMaxChunks * kTileBytes + 64;
+  // X tile (chunks boxes of 128 rows) + R tile (kNB * chunks boxes of 64
+  // rows) + barriers: 97 KB for float rows of 512 B, so two CTAs share an
+  // SM and one's epilogue overlaps the other's copies and MMAs
+  const size_t smem = 1024 + (size_t)a.chunks * (kTileBytes + kNB * kBTileBytes) + 64;
   auto kern = bf16 ? project_tc_kernel<true> : project_tc_kernel<false>;
   MSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned grid = (unsigned)((n + kRows - 1) / kRows);
