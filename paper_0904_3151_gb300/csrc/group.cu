@@ -175,8 +175,14 @@ hist_kernel(SortArgs a) {
     bool valid = e < cnt;
     uint32_t digit = 0xFFFFFFFFu;
     if (valid) digit = (uint32_t)(load_key<KeyT, FROM_STR>(a, kl, seg, base + e) >> a.shift) & 0xFFu;
-    unsigned peers = __match_any_sync(0xffffffffu, digit);
-    if (valid && lane == __ffs(peers) - 1) h[warp][digit] += __popc(peers);
+    // a warp whose 32 items share one digit (runs of equal keys) counts it
+    // with one add; otherwise every item adds itself (distinct bins mostly)
+    const uint32_t d0 = __shfl_sync(0xffffffffu, digit, 0);
+    if (__all_sync(0xffffffffu, digit == d0)) {
+      if (lane == 0 && valid) h[warp][d0] += 32u;
+    } else if (valid) {
+      atomicAdd(&h[warp][digit], 1u);
+    }
     __syncwarp();
   }
   __syncthreads();
