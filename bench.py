@@ -47,6 +47,8 @@ def parse():
                     help="skip the bf16, learned-projection and batched forms")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision form")
+    ap.add_argument("--no-learned8m", action="store_true",
+                    help="skip the 8M learned-projection configuration")
     return ap.parse_args()
 
 
@@ -62,6 +64,98 @@ def time_steps(fn, steps, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps, out
+
+
+def train_projection(msm, Xt, eps, ell, k, d, seed, n_pairs=1 << 21, steps=1000):
+    """Train the MLP feature map on a sample Xt (device): positives are the
+    pairs the plain method finds there (Q = 4), negatives random pairs
+    farther than eps.  Returns (net, seconds, first and last loss)."""
+    import torch
+    t0 = time.perf_counter()
+    n = Xt.shape[0]
+    pos, _, _ = msm.eps_graph(Xt, msm.COSINE, eps, ell, k, d, Q=4, seed=seed,
+                              out_mode=1, cand_capacity=800 * n)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    npos = min(pos.numel(), n_pairs)
+    P = pos[torch.randint(0, pos.numel(), (npos,), device="cuda", generator=g)]
+    del pos
+    ri = torch.randint(0, n, (3 * npos,), device="cuda", generator=g)
+    rj = torch.randint(0, n, (3 * npos,), device="cuda", generator=g)
+    Xn = torch.nn.functional.normalize(Xt.float(), dim=1)
+    far = (ri != rj) & (1.0 - (Xn[ri] * Xn[rj]).sum(1) > eps)
+    ri, rj = ri[far][:npos], rj[far][:npos]
+    pi = torch.cat([P >> 32, ri]).to(torch.int32).contiguous()
+    pj = torch.cat([P & 0xFFFFFFFF, rj]).to(torch.int32).contiguous()
+    lab = torch.cat([torch.ones(npos, dtype=torch.uint8, device="cuda"),
+                     torch.zeros(ri.numel(), dtype=torch.uint8, device="cuda")])
+    net = msm.MLPProjection(Xt.shape[1], 512, 128, seed=0)
+    hist = net.train(Xt, pi, pj, lab, steps=steps, batch=8192, lr=1e-2, m_pos=0.999, m_neg=0.2)
+    torch.cuda.synchronize()
+    return net, time.perf_counter() - t0, (float(hist[0]), float(hist[-1]))
+
+
+def run_learned_8m(msm, steps, stream, n_sample=400_000):
+    """The learned-projection configuration: an MLP 128-512-128 (gelu, bf16
+    weights) trained on a disjoint 1M sample of a 10,000-cluster mixture,
+    then the graph of 8,000,000 bf16 vectors of the same mixture with
+    l = 96, k = 8, d = 4, cosine eps = 0.1.  Plain (random projection of x)
+    and learned forms each take the smallest Q whose missing ratio, measured
+    exhaustively among the pairs of a random point sample, is <= 1e-6."""
+    import torch
+    wl = W.WORKLOADS["learned"]
+    Xb = torch.from_numpy(W.to_bf16_values(W.clustered(
+        wl.n, wl.dim, wl.n_clusters, wl.sigma, wl.data_seed))).cuda().to(torch.bfloat16)
+    Xt = torch.from_numpy(W.clustered(1_000_000, wl.dim, wl.n_clusters, wl.sigma,
+                                      wl.data_seed + 500, centres_seed=wl.data_seed)).cuda()
+    net, train_s, losses = train_projection(msm, Xt, wl.eps, wl.ell, wl.k, wl.d, wl.r_seed + 1)
+    del Xt
+    g = torch.Generator(device="cuda").manual_seed(5)
+    perm = torch.randperm(wl.n, device="cuda", generator=g)[:n_sample]
+    mark = torch.zeros(wl.n, dtype=torch.bool, device="cuda")
+    mark[perm] = True
+    truth = msm.eps_count_exhaustive(Xb[perm].contiguous(), msm.COSINE, wl.eps)
+    cap = 500 * wl.n
+
+    def run(Q, learned):
+        Y = net.features(Xb) if learned else None
+        return msm.eps_graph(Xb, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=Q, seed=wl.r_seed,
+                             out_mode=msm.OUT_PAIRS, cand_capacity=cap, Y=Y)
+
+    def ratio(p):
+        found = 0
+        for c0 in range(0, p.numel(), 1 << 28):      # bounded temporaries
+            c = p[c0:c0 + (1 << 28)]
+            found += int((mark[c >> 32] & mark[c & 0xFFFFFFFF]).sum().item())
+        return (truth - found) / max(1, truth)
+
+    out = {}
+    for name, learned, q0 in (("plain", False, 6), ("learned", True, 2)):
+        ladder, chosen = [], None
+        for Q in range(q0, 25):
+            p, _, _ = run(Q, learned)
+            r = ratio(p)
+            del p
+            ladder.append({"Q": Q, "missing_ratio_sampled": r})
+            if r <= 1e-6:
+                chosen = Q
+                break
+        if chosen is None:
+            out[name] = {"Q_ladder": ladder, "note": "no Q <= 24 reached 1e-6"}
+            continue
+        ms, (p, _, st) = time_steps(lambda: run(chosen, learned), steps, stream)
+        out[name] = {"value": wl.n / (ms / 1000.0), "ms_per_step": ms, "Q": chosen,
+                     "missing_ratio_sampled": ratio(p), "pairs": st["count"],
+                     "Q_ladder": ladder}
+        del p
+    res = {"unit": UNIT, "points": wl.n, "train_seconds": train_s, "train_loss": list(losses),
+           "missing_sample": f"{truth:,} true pairs among {n_sample:,} random points",
+           "plain": out.get("plain"), "learned": out.get("learned"),
+           "note": "l = 96, k = 8, d = 4; step of the learned form = MLP features + graph"}
+    if "value" in out.get("plain", {}) and "value" in out.get("learned", {}):
+        res["value"] = out["learned"]["value"]
+        res["speedup_vs_plain"] = out["plain"]["ms_per_step"] / out["learned"]["ms_per_step"]
+    del Xb
+    return res
 
 
 def run_forms(msm, wl, X, Xh, n, Q, seed, truth, ratio_plain, ms_plain, steps, stream):
@@ -709,6 +803,8 @@ def main():
         forms["lsh_d0"] = run_lsh_d0(msm, X, wl, n, missing["truth_pairs"], 1, stream)
         forms["auto_params"] = run_auto_params(msm, X, wl, n, missing["truth_pairs"], 2, stream)
         forms["e2lsh"] = run_e2lsh(msm, X, wl, n, ms, stream)
+        if not a.no_learned8m:
+            forms["learned_8m"] = run_learned_8m(msm, 2, stream)
         forms["output_sensitivity"] = run_output_sensitivity(msm, wl, Q, stream)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
