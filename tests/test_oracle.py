@@ -425,3 +425,12 @@ def test_choose_params_is_minimal(n, p, S):
     assert Q <= limit and Q == oracle.solve_Q(ell, d, p, 1e-6)
     if d > 0:  # one mismatch fewer needs more replicates than allowed
         assert oracle.solve_Q(ell, d - 1, p, 1e-6) > limit
+
+
+def test_choose_params_replicate_budget_is_24():
+    """n = 1024 (l = 20), p = 0.1434, large S: P(Binom(20, p) <= 2) =
+    0.8566^20 + 20 p 0.8566^19 + 190 p^2 0.8566^18 = 0.0452 + 0.1514 + 0.2407
+    = 0.4373, so d = 2 needs Q = ceil(13.8155 / 0.5750) = 25 -- one more than
+    the budget (below 25) allows; the rule moves on to d = 3."""
+    assert oracle.solve_Q(20, 2, 0.1434, 1e-6) == 25
+    assert oracle.choose_params(1024, 0.1434, 1e-6, 1e9) == (20, 6, 3, 13)
