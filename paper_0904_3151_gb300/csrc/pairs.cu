@@ -731,6 +731,43 @@ __device__ __forceinline__ bool gaps_differ(const uint32_t (&fa)[FP],
   return bad == 0;
 }
 
+// Gap test of one tile row against the tile's columns, over the first NW
+// field words only (the words above the highest gap block hold no gap
+// field).  Diagonal tile: round robin -- in step s lane l pairs with column
+// (l + s) mod 32; steps 1..15 and the lower half of step 16 cover every
+// unordered pair of the block exactly once with all lanes busy.
+template <int FP, int NW>
+__device__ __forceinline__ uint32_t tile_gaps_n(bool diag, const uint32_t (&fa)[FP],
+                                                const uint32_t (*sf)[FP],
+                                                const uint32_t (&gapf)[FP], uint32_t ncols,
+                                                int lane) {
+  uint32_t gpass = 0;
+  if (diag) {
+#pragma unroll 4
+    for (int s = 1; s <= 16; ++s) {
+      const int c = (lane + s) & 31;
+      const bool ok = (s < 16 || lane < 16) && gaps_differ<FP, NW>(fa, sf[c], gapf);
+      gpass |= (uint32_t)ok << c;
+    }
+  } else {
+#pragma unroll 4
+    for (uint32_t c = 0; c < ncols; ++c)
+      gpass |= (uint32_t)gaps_differ<FP, NW>(fa, sf[c], gapf) << c;
+  }
+  return gpass;
+}
+
+template <int FP, int N>
+__device__ __forceinline__ uint32_t tile_gaps(int nw, bool diag, const uint32_t (&fa)[FP],
+                                              const uint32_t (*sf)[FP],
+                                              const uint32_t (&gapf)[FP], uint32_t ncols,
+                                              int lane) {
+  if constexpr (N > 0) {
+    if (nw < N) return tile_gaps<FP, N - 1>(nw, diag, fa, sf, gapf, ncols, lane);
+  }
+  return tile_gaps_n<FP, N>(diag, fa, sf, gapf, ncols, lane);
+}
+
 // Hamming (differing symbols) <= d and (hashed keys only) all kept fields
 // equal.
 template <int FP, int FU>
@@ -794,7 +831,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
   const uint32_t* pool = fields + (size_t)a.q * a.n * FP;
   FuseAcc acc;
   uint32_t cur_g = 0xffffffffu;
-  int cur_seg = -1, subw = 0;
+  int cur_seg = -1, subw = 0, nw = 0;
   bool hashed = false;
   uint32_t gapf[FP], keepf[FP];
 #pragma unroll
@@ -824,6 +861,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
       // gap blocks: below the highest kept block and not kept
       const uint32_t K = md.K;
       const uint32_t Gs = ((1u << md.maxK) - 1u) & ~K;
+      nw = Gs ? (31 - __clz(Gs)) / 2 + 1 : 0;  // words up to the highest gap block
 #pragma unroll
       for (int w = 0; w < FP; ++w) {
         gapf[w] = ((Gs >> (2 * w)) & 1u ? 0x8000u : 0u) |
@@ -848,6 +886,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
       }
       __syncwarp();
       const int P = (int)(len * (len - 1) / 2);
+      uint32_t npass = 0;  // passing pairs, compacted into sm_qs (non-fused)
       for (int r = 0; r < P; r += 32) {
         const int p = r + lane;
         bool pass = false;
@@ -869,11 +908,20 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
           continue;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, pass);
-        if (bal) {
-          unsigned long long b0 = 0;
-          if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)__popc(bal));
-          b0 = __shfl_sync(0xffffffffu, b0, 0) + __popc(bal & ((1u << lane) - 1u));
-          if (pass && b0 < (unsigned long long)a.cap) a.cand[b0] = ordered_pair(ii, jj);
+        if (pass) sm_qs[warp][npass + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)p;
+        npass += __popc(bal);
+      }
+      if (!FUSE && npass) {
+        // one append per work item: its pairs lie together in E, so the
+        // recheck finds their (at most 32) rows in L1
+        __syncwarp();
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)npass);
+        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        for (uint32_t t = lane; t < npass; t += 32) {
+          const uint32_t p = sm_qs[warp][t];
+          const uint32_t ii = sm_i[warp][tri_a[p]], jj = sm_i[warp][tri_b[p]];
+          if (b0 + t < (unsigned long long)a.cap) a.cand[b0 + t] = ordered_pair(ii, jj);
         }
       }
       __syncwarp();
@@ -919,30 +967,18 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
       __syncwarp();
       const uint32_t ncols = min(32u, len - (uint32_t)(J * 32));
       const uint32_t colmask = ncols == 32 ? 0xffffffffu : ((1u << ncols) - 1u);
-      uint32_t gpass = 0;
-      if (I == J) {
-        // Diagonal tile: round robin -- in step s lane l pairs with column
-        // (l + s) mod 32; steps 1..15 and the lower half of step 16 cover
-        // every unordered pair of the block exactly once with all lanes busy.
-#pragma unroll 4
-        for (int s = 1; s <= 16; ++s) {
-          const int c = (lane + s) & 31;
-          const bool ok = (s < 16 || lane < 16) && gaps_differ<FP, FU>(fa, sm_f[warp][c], gapf);
-          gpass |= (uint32_t)ok << c;
-        }
-      } else {
-#pragma unroll 4
-        for (uint32_t c = 0; c < ncols; ++c)
-          gpass |= (uint32_t)gaps_differ<FP, FU>(fa, sm_f[warp][c], gapf) << c;
-      }
+      uint32_t gpass = tile_gaps<FP, FU>(nw, I == J, fa, sm_f[warp], gapf, ncols, lane);
       gpass &= va ? colmask : 0u;
       // Survivors of the gap test (~5 % of the pairs) take the Hamming, kept-
       // block and replicate tests.  The replicate test reads earlier pools
       // from global memory, so the survivors of the whole tile are queued
       // once in shared memory and tested 32 at a time, one per lane: the
       // loads of 32 pairs are in flight together instead of each lane
-      // walking its own survivors one dependent load after another.  Each
-      // round appends its passing pairs with one warp-aggregated atomic.
+      // walking its own survivors one dependent load after another.  The
+      // passing pairs are compacted to the front of the same queue (a round
+      // writes only entries already read) and the tile appends them to E
+      // with one atomic, so they lie together there: the recheck then finds
+      // the tile's (at most 64) rows in L1.
       uint32_t cnt = __popc(gpass), incl = cnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -954,6 +990,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
 #pragma unroll
         for (int w = 0; w < FP; ++w) sm_fr[warp][lane][w] = fa[w];
         sm_ir[warp][lane] = ia;
+        uint32_t npass = 0;
         uint32_t m = gpass, pos = incl - cnt;
         while (m) {
           const int c = __ffs(m) - 1;
@@ -982,12 +1019,20 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
             fuse_one(a, ok, ii, jj, lane, sm_q[warp], acc);
           } else {
             const unsigned bal = __ballot_sync(0xffffffffu, ok);
-            if (bal) {
-              unsigned long long b1 = 0;
-              if (lane == 0) b1 = atomicAdd(a.count, (unsigned long long)__popc(bal));
-              b1 = __shfl_sync(0xffffffffu, b1, 0) + __popc(bal & ((1u << lane) - 1u));
-              if (ok && b1 < (unsigned long long)a.cap) a.cand[b1] = ordered_pair(ii, jj);
-            }
+            __syncwarp();
+            if (ok) sm_qs[warp][npass + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((r << 5) | c);
+            npass += __popc(bal);
+          }
+        }
+        if (!FUSE && npass) {
+          __syncwarp();
+          unsigned long long b1 = 0;
+          if (lane == 0) b1 = atomicAdd(a.count, (unsigned long long)npass);
+          b1 = __shfl_sync(0xffffffffu, b1, 0);
+          for (uint32_t t = lane; t < npass; t += 32) {
+            const uint32_t e = sm_qs[warp][t];
+            const uint32_t ii = sm_ir[warp][e >> 5], jj = sm_i[warp][e & 31u];
+            if (b1 + t < (unsigned long long)a.cap) a.cand[b1 + t] = ordered_pair(ii, jj);
           }
         }
       }

@@ -10,8 +10,12 @@ namespace {
 
 using namespace dist;
 constexpr int kThreads = 256;
+constexpr int kCtasPerSm = 4;  // resident CTAs of recheck_kernel per SM
 
-// 8 pairs per warp (4 lanes each), grid-stride over the candidates.
+// 8 pairs per warp (4 lanes each).  Each CTA walks one contiguous range of
+// E, 64 pairs at a time: the pair check appends the pairs of a tile
+// together, so the rows of a tile (at most 64 points) are read from HBM or
+// L2 once and then hit in L1 for the rest of its pairs.
 __global__ void __launch_bounds__(kThreads)
 recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
                float eps, const float* nrm, const uint64_t* cand,
@@ -22,12 +26,13 @@ recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
   int64_t m = m_max;
   if (m_dev) m = min(m, (int64_t)*m_dev);
   const int lane = threadIdx.x & 31, sl = lane & (G - 1), grp = lane / G;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  constexpr int kPerIter = kThreads / G;
+  const int64_t per = ((m + gridDim.x - 1) / gridDim.x + kPerIter - 1) / kPerIter * kPerIter;
+  const int64_t c0 = (int64_t)blockIdx.x * per, c1 = min(m, c0 + per);
   unsigned long long nre = 0;
-  for (int64_t base = warp * (32 / G); base < m; base += nwarps * (32 / G)) {
+  for (int64_t base = c0 + (threadIdx.x >> 5) * (32 / G); base < c1; base += kPerIter) {
     const int64_t t = base + grp;
-    const bool valid = t < m;
+    const bool valid = t < c1;
     const uint64_t pr = valid ? cand[t] : 0;
     const int64_t i = (int64_t)(pr >> 32), j = (int64_t)(pr & 0xffffffffu);
     const float S = group_sq_dist<G>(X, dtype, valid ? i : 0, valid ? j : 0, dim, sl);
@@ -134,9 +139,12 @@ int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
   if (m_max <= 0) return MSM_OK;
   const int64_t warps = (m_max + 7) / 8;
   int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
-  const int64_t cap = (int64_t)num_sms() * 8;
+  const int64_t cap = (int64_t)num_sms() * kCtasPerSm;
   if (grid > cap) grid = cap;
   const float relS = 10.f * (float)kU;
+  // no shared memory: let L1 take the whole on-chip store for the rows
+  MSM_CUDA(cudaFuncSetAttribute(recheck_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxL1));
   kt_begin(KC_RECHECK, s);
   recheck_kernel<<<(int)grid, kThreads, 0, s>>>(X, dtype, n, dim, metric, eps, nrm, cand,
                                                 m_dev, m_max, pairs_out, dist_out,
