@@ -120,7 +120,7 @@ __device__ __forceinline__ double decide(const void* X, int dtype, int64_t i,
   return delta;
 }
 
-// Sum of squared differences of rows i and j by the 8 lanes of a group.
+// Compensated (Kahan) addition of v to acc; comp carries the lost low part.
 __device__ __forceinline__ void kahan_add(float v, float& acc, float& comp) {
   const float y = v - comp;
   const float s = acc + y;

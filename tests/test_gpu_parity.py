@@ -166,6 +166,38 @@ def test_enumerate_one_large_group(msm):
         assert np.array_equal(_u64(pairs), np.sort(want))
 
 
+@pytest.mark.parametrize("seed,ell,k,d,probs", [
+    (1, 64, 8, 4, [0.02, 0.1, 0.3, 0.5, 0.5, 0.3, 0.1, 0.02]),
+    (2, 64, 8, 4, [0.5, 0.05, 0.2, 0.02, 0.4, 0.1, 0.3, 0.5]),
+    (3, 40, 10, 6, [0.15] * 10),
+    (4, 40, 10, 6, [0.4, 0.03, 0.25, 0.1, 0.5, 0.05, 0.2, 0.3, 0.02, 0.45]),
+])
+def test_enumerate_subkey_groups(msm, seed, ell, k, d, probs):
+    """Long runs split into first-gap-block groups of every size: block b of
+    a string is a fixed value with its lowest bit flipped with probability
+    probs[b], so the Hamming distance is the number of differing blocks and
+    runs of equal kept blocks hold hundreds of members whose first gap block
+    takes two values in sorted order -- tiles with uniform rows, uniform
+    columns, two groups on the diagonal and mixed groups all occur."""
+    n = 1200
+    rng = np.random.default_rng(seed)
+    lo = [b * ell // k for b in range(k)]
+    S = np.zeros((1, n, 1), dtype=np.uint64)
+    for b in range(k):
+        width = (b + 1) * ell // k - lo[b]
+        v = np.uint64(rng.integers(0, 1 << width))
+        flip = (rng.random(n) < probs[b]).astype(np.uint64)
+        S[0, :, 0] |= (v ^ flip) << np.uint64(lo[b])
+    pairs, st = msm.enumerate_pairs(_t(S.view(np.int64)), ell, k, d, canonical=True)
+    want, ost = oracle.msm(S, ell, k, d)
+    assert len(want) > 10000
+    assert np.array_equal(_u64(pairs), want)
+    if _keys_exact(ell, k, d):
+        assert st["checks"] == ost["checks"]
+    else:
+        assert st["checks"] >= ost["checks"]
+
+
 def test_enumerate_unordered_matches(msm):
     S = W.random_strings(3000, 64, 2, 9, n_centres=30, flip=0.05)
     pairs, _ = msm.enumerate_pairs(_t(S.view(np.int64)), 64, 8, 4, canonical=False)
