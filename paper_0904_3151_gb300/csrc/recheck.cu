@@ -11,11 +11,17 @@ namespace {
 using namespace dist;
 constexpr int kThreads = 256;
 constexpr int kCtasPerSm = 4;  // resident CTAs of recheck_kernel per SM
+constexpr int kStage = 128;    // kept pairs staged per warp before one append
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 // 8 pairs per warp (4 lanes each).  Each CTA walks one contiguous range of
 // E, 64 pairs at a time: the pair check appends the pairs of a tile
 // together, so the rows of a tile (at most 64 points) are read from HBM or
-// L2 once and then hit in L1 for the rest of its pairs.
+// L2 once and then hit in L1 for the rest of its pairs.  Kept pairs are
+// staged per warp in shared memory and appended kStage at a time: one
+// atomic on the output counter per 8 pairs serialised the whole kernel on
+// that one address.
 __global__ void __launch_bounds__(kThreads)
 recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
                float eps, const float* nrm, const uint64_t* cand,
@@ -23,6 +29,22 @@ recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
                uint64_t* pairs_out, float* dist_out, unsigned long long* count,
                unsigned long long* recompute, float relS) {
   constexpr int G = 4;  // lanes per pair: 8 pairs per warp in flight
+  __shared__ uint64_t st_p[kThreads / 32][kStage];
+  __shared__ float st_d[kThreads / 32][kStage];
+  const int wb = threadIdx.x >> 5;
+  uint32_t ns = 0;  // pairs staged by this warp
+  auto flush = [&]() {
+    __syncwarp();
+    unsigned long long b0 = 0;
+    if (lane_id() == 0) b0 = atomicAdd(count, (unsigned long long)ns);
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    for (uint32_t q = lane_id(); q < ns; q += 32) {
+      if (pairs_out) pairs_out[b0 + q] = st_p[wb][q];
+      if (dist_out) dist_out[b0 + q] = st_d[wb][q];
+    }
+    __syncwarp();
+    ns = 0;
+  };
   int64_t m = m_max;
   if (m_dev) m = min(m, (int64_t)*m_dev);
   const int lane = threadIdx.x & 31, sl = lane & (G - 1), grp = lane / G;
@@ -45,17 +67,15 @@ recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
       nre += exact;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (bal) {
-      unsigned long long b0 = 0;
-      if (lane == 0) b0 = atomicAdd(count, (unsigned long long)__popc(bal));
-      b0 = __shfl_sync(0xffffffffu, b0, 0);
-      if (keep) {
-        const unsigned long long slot = b0 + __popc(bal & ((1u << lane) - 1u));
-        if (pairs_out) pairs_out[slot] = pr;
-        if (dist_out) dist_out[slot] = (float)delta;
-      }
+    if (keep) {
+      const uint32_t pos = ns + __popc(bal & ((1u << lane) - 1u));
+      st_p[wb][pos] = pr;
+      st_d[wb][pos] = (float)delta;
     }
+    ns += __popc(bal);
+    if (ns > (uint32_t)(kStage - 32 / G)) flush();  // room for one more iteration
   }
+  if (ns) flush();
   if (nre) atomicAdd(recompute, nre);
 }
 
@@ -142,9 +162,6 @@ int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
   const int64_t cap = (int64_t)num_sms() * kCtasPerSm;
   if (grid > cap) grid = cap;
   const float relS = 10.f * (float)kU;
-  // no shared memory: let L1 take the whole on-chip store for the rows
-  MSM_CUDA(cudaFuncSetAttribute(recheck_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                (int)cudaSharedmemCarveoutMaxL1));
   kt_begin(KC_RECHECK, s);
   recheck_kernel<<<(int)grid, kThreads, 0, s>>>(X, dtype, n, dim, metric, eps, nrm, cand,
                                                 m_dev, m_max, pairs_out, dist_out,
