@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import itertools
 import json
 import os
 import subprocess
@@ -545,6 +546,19 @@ KERNEL_SOURCES = {
 }
 
 
+def gap_words_mean(k, d):
+    """Mean, over the C(k, d) kept-block sets K of the first-mask rule (the
+    k - d kept blocks), of the 32-bit field words up to the one holding the
+    highest gap block (a block below max K that is not kept); two 16-bit
+    block fields share a word.  These are the words the gap test reads."""
+    tot = cnt = 0
+    for K in itertools.combinations(range(k), k - d):
+        gaps = [b for b in range(max(K)) if b not in K]
+        tot += gaps[-1] // 2 + 1 if gaps else 0
+        cnt += 1
+    return tot / cnt
+
+
 def kernel_source_hash(kind="pair_check"):
     h = hashlib.sha256()
     for f in sorted(KERNEL_SOURCES.get(kind, os.listdir(
@@ -761,19 +775,22 @@ def main():
         # integer-ALU bound: pair inspections per second against the
         # issue-rate ceiling derived in the design notes
         # unit: one pair inside a group; algorithmic work per pair in the
-        # field layout = 3 integer ops per 32-bit word of fields (xor, add,
-        # lop3) x ceil(k/2) words + 1 compare
+        # field layout = 3 integer ops (xor, add, lop3) per 32-bit word of
+        # fields up to the one holding the highest gap block (mean over the
+        # kept-block sets) + 1 compare
         checks = st["checks"]
         avg_ms = kms[dom] / klaunch[dom]
         per_launch = checks / max(1, klaunch[dom] // a.steps)
         ach = per_launch / (avg_ms / 1000.0) / 1e9
-        ops_per_check = 3 * ((wl.k + 1) // 2) + 1
+        ops_per_check = 3 * gap_words_mean(wl.k, wl.d) + 1
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
         peak = sm_count * 128 * peaks["sm_max_mhz"] * 1e6 / ops_per_check / 1e9
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "Gpairs/s", "frac": ach / peak, "traffic": traffic_for(dom, "scale"),
                 "peak_source": f"derived: {sm_count} SMs x 128 int32 lanes x "
-                               f"{peaks['sm_max_mhz']:.0f} MHz / {ops_per_check} ops per in-group pair"}
+                               f"{peaks['sm_max_mhz']:.0f} MHz / {ops_per_check:.2f} ops per in-group "
+                               f"pair (3 per field word up to the highest gap block, mean over "
+                               f"the kept-block sets, + 1)"}
     elif dom == "project":
         flops = 2.0 * n * wl.dim * Q * wl.ell
         avg_ms = kms[dom] / klaunch[dom]
