@@ -15,6 +15,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -41,6 +42,8 @@ def parse():
     ap.add_argument("--clusters", type=int, default=0,
                     help="override the number of clusters (0 = workload's)")
     ap.add_argument("--cpu-sample", type=int, default=20000)
+    ap.add_argument("--clocks-dir", default="",
+                    help="folder for the raw nvidia-smi clock samples (default: temp dir)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-missing", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -245,8 +248,6 @@ def run_batched(msm, steps, stream):
     autotuner.  Both draw R from the same seed (identical strings), so their
     counts, and missing-edge ratios, are identical; Q is the smallest from 7
     up whose measured ratio is <= 1e-6."""
-    import tempfile
-
     import torch
     wl = W.WORKLOADS["batched"]
     sizes = W.set_sizes(wl.n_sets, wl.set_min, wl.set_max, wl.data_seed)
@@ -485,9 +486,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, out_dir: str = ""):
         self.idx = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(out_dir or tempfile.gettempdir(), f"clocks_rank{gpu_index}.csv")
         self.proc = None
 
     def start(self):
@@ -684,7 +685,7 @@ def main():
         del p, dv
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, a.clocks_dir)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
