@@ -734,34 +734,54 @@ def main():
     value = replicas.job_throughput(world, n, ms)
     pairs_per_s = world * counts[-1] / (ms / 1000.0)
 
-    # ---- e2e: host X in, host pairs out, through the same API
+    # ---- e2e: host X in, host pairs out, through the same API.  Each step
+    # is one msm_eps_graph call on pinned host X (the library copies it in)
+    # followed by the device->host read of its pairs and distances into
+    # pinned host buffers.  The read of step r runs on a second stream while
+    # step r + 1 computes (two host buffer pairs, alternating), as a stream
+    # of jobs would run; the timed region ends when the last read lands.
     e2e = None
     if not a.no_e2e:
         Xpin = torch.from_numpy(Xh).pin_memory()
         reps = max(2, min(3, a.steps))
         p, dv, st = step(Xpin)          # warm
-        out_p = torch.empty(p.numel(), dtype=torch.int64, pin_memory=True)
-        out_d = torch.empty(dv.numel(), dtype=torch.float32, pin_memory=True)
+        cap = p.numel()  # the same input gives the same pairs every step
+        host = [(torch.empty(cap, dtype=torch.int64, pin_memory=True),
+                 torch.empty(cap, dtype=torch.float32, pin_memory=True)) for _ in range(2)]
         del p, dv
+        side = torch.cuda.Stream()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         bo = 0
-        for _ in range(reps):
+        for r in range(reps):
             p, dv, st = step(Xpin)
-            if out_p.numel() < p.numel():
-                out_p = torch.empty(p.numel(), dtype=torch.int64, pin_memory=True)
-                out_d = torch.empty(dv.numel(), dtype=torch.float32, pin_memory=True)
-            out_p[:p.numel()].copy_(p, non_blocking=True)
-            out_d[:dv.numel()].copy_(dv, non_blocking=True)
-            bo = p.numel() * 8 + dv.numel() * 4
+            m = p.numel()
+            if m > cap:  # not expected: the same input gives the same count
+                side.synchronize()
+                cap = m
+                host = [(torch.empty(cap, dtype=torch.int64, pin_memory=True),
+                         torch.empty(cap, dtype=torch.float32, pin_memory=True))
+                        for _ in range(2)]
+            ready = torch.cuda.Event()
+            ready.record(stream)
+            side.wait_event(ready)
+            hp, hd = host[r % 2]
+            with torch.cuda.stream(side):
+                hp[:m].copy_(p, non_blocking=True)
+                hd[:m].copy_(dv, non_blocking=True)
+            p.record_stream(side)
+            dv.record_stream(side)
+            bo = m * 8 + dv.numel() * 4
             del p, dv
+        stream.wait_stream(side)
         f1.record(stream)
         torch.cuda.synchronize()
         ems = replicas.max_over_ranks(f0.elapsed_time(f1) / reps, dist, "cuda")
         e2e = {"value": replicas.job_throughput(world, n, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(Xh.nbytes), "d2h_bytes_per_step": int(bo),
-               "ms_per_step": ems}
+               "ms_per_step": ems, "steps": reps,
+               "overlap": "device->host read of step r on a second stream during step r+1"}
 
     # ---- roofline of the dominant kernel class
     peaks = measured_peaks()
