@@ -456,7 +456,7 @@ def run_auto_params(msm, X, wl, n, truth, steps, stream, gamma=1e-6):
 
 
 def run_output_sensitivity(msm, wl, Q, stream, sizes=(125_000, 250_000, 500_000, 1_000_000)):
-    """Sec. 5.4 / Fig. 7: time per 10,000 output pairs as n grows (same
+    """Sec. 5.4 / Fig. 7: milliseconds per 10^4 reported pairs as n grows (same
     cluster size, so the output grows with n)."""
     import torch
     rows = []

@@ -1,8 +1,8 @@
 """Learned projection (MLP feature map) -- CPU oracle.
 
 TEST INFRASTRUCTURE ONLY.  The paper suggests replacing the random
-projection by a non-random hashing (Sec. 6: "combine MSM with other
-non-random hashing methods"); the learned form maps every point through
+projection by a non-random hashing (Sec. 6 names learned hash functions as
+a drop-in for the random projection); the learned form maps every point through
   y = W2 . gelu(W1 . x + b1) + b2        (D -> H -> D_y)
 and then takes the usual sign projection (Eq. 3) of y.  Training pulls
 epsilon-neighbour pairs together and pushes other pairs apart in angle:

@@ -14,7 +14,7 @@
  *     W = ceil(ell / 64); unused high bits are zero.
  *   - sign(t) is 1 iff t > 0 (Eq. 3), so t == 0 gives 0.
  *   - block b (0-based) of a string covers bits [floor(b*ell/k),
- *     floor((b+1)*ell/k)) ("approximately equal length", Sec. 2.2).
+ *     floor((b+1)*ell/k)) (Sec. 2.2 asks only for blocks of nearly the same size).
  *   - a pair co-grouped under kept block set K is reported under K only if
  *     K is the set of its k-d lowest-index equal blocks (the per-mask
  *     de-duplication Sec. 2.2 leaves to the original MSM paper), and only in
@@ -354,9 +354,9 @@ int64_t orc_eps_bruteforce(const double* X, int64_t n, int D, int metric,
 }
 
 /* ========================================================================
- * E2LSH symbol strings (Sec. 3.1: LSH maps a vector to a string of
- * integers; the Euclidean family of Datar et al. 2004, which Sec. 4.3 tunes
- * by its width w).
+ * E2LSH symbol strings (Sec. 3.1: an LSH family turns each vector into a
+ * sequence of integer symbols; here the Euclidean family of Datar et al.
+ * 2004, whose width w Sec. 4.3 tunes).
  * ---------------------------------------------------------------------- */
 
 /* Offsets of the buckets: u_{q,c} in [0, 1), one per (replicate, symbol):
