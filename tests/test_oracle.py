@@ -237,6 +237,27 @@ def test_msm_group_checks_count(ell, k, d, Q, n, nc, flip):
     assert st["checks"] == total
 
 
+@pytest.mark.parametrize("ell,k,d,Q,n,nc,flip", CASES[:6])
+def test_msm_checks_equal_pairwise_block_agreements(ell, k, d, Q, n, nc, flip):
+    """The same count seen pair by pair: a pair shares a group under kept set
+    K iff all blocks of K agree, so it is inspected C(e, k - d) times in a
+    replicate where e of its k blocks agree (Sec. 2.2); summed over pairs and
+    replicates this must equal the oracle's count of in-group inspections."""
+    S = W.random_strings(n, ell, Q, 17 * ell + k + d, n_centres=nc, flip=flip)
+    _, st = oracle.msm(S, ell, k, d)
+    bounds = [(b * ell // k, (b + 1) * ell // k) for b in range(k)]
+    iu, ju = np.triu_indices(n, 1)
+    total = 0
+    for q in range(Q):
+        bits = np.unpackbits(S[q].view(np.uint8), axis=1, bitorder="little")[:, :ell]
+        e = np.zeros(len(iu), dtype=np.int64)
+        for lo, hi in bounds:
+            e += np.all(bits[iu, lo:hi] == bits[ju, lo:hi], axis=1)
+        binom = np.array([math.comb(v, k - d) for v in range(k + 1)], dtype=np.int64)
+        total += int(binom[e].sum())
+    assert st["checks"] == total
+
+
 def test_msm_d0_is_equivalence_classes():
     """d = 0 (Sec. 2.1, Fig. 1): pairs of identical strings."""
     S = W.random_strings(500, 48, 1, 3, n_centres=40, flip=0.0)
