@@ -1,5 +1,5 @@
 """Host-side pieces of bench.py's roofline (no GPU): the word count of the
-pair check's ALU model."""
+pair check's ALU model and the algorithmic bytes of the HBM-bound kernels."""
 import importlib.util
 import os
 
@@ -33,3 +33,24 @@ def test_gap_words_bounds(bench):
             m = bench.gap_words_mean(k, d)
             assert 0 <= m <= (k + 1) // 2
     assert bench.gap_words_mean(8, 0) == 0
+
+
+def test_algorithmic_bytes_hand_counts(bench):
+    # one replicate batch of the scale workload: 210 kept sets x n items,
+    # strings of W = 2 words, 4 radix passes of 8-bit digits over 32-bit keys
+    st = {"masks": 12 * 210, "cand": 1000}
+    n = 1000
+    items = 210 * n
+    # scatter: pass 0 reads the 16-byte string and writes key + index (8 B),
+    # passes 1-3 read and write key + index (16 B): (16 + 8 + 48) / 4 = 18 B
+    b, unit, bound = bench.algorithmic("radix_scatter", st, n, 128, 12, 2, 4)
+    assert (b, unit, bound) == (items * 18, "GB/s", "hbm")
+    # histogram: pass 0 reads the string (16 B), passes 1-3 the key (4 B):
+    # (16 + 12) / 4 = 7 B
+    b, _, _ = bench.algorithmic("radix_hist", st, n, 128, 12, 2, 4)
+    assert b == items * 7
+    # recheck: the pair (8 B), two float rows of 128 (1024 B), pair and
+    # distance out (12 B)
+    b, _, _ = bench.algorithmic("recheck", st, n, 128, 12, 2, 4)
+    assert b == 1000 * (8 + 1024 + 12)
+    assert bench.algorithmic("pair_check", st, n, 128, 12, 2, 4) == (None, None, None)
