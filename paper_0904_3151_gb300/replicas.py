@@ -1,9 +1,10 @@
 """Multi-GPU layout of the method: independent replicas (weak scaling).
 
-The method has no exchange step on one point set that this build runs
-across GPUs: every rank (one process per GPU) owns an independent point set
-of the same workload and runs the whole method on it; the only collective
-is the timing reduction.  Host-side logic only (no kernels here).
+The library runs the method for one point set on one GPU, so several GPUs
+serve as independent replicas: every rank (one process per GPU) owns an
+independent point set of the same workload and runs the whole method on it;
+the only collective is the timing reduction.  Host-side logic only (no
+kernels here).
 """
 from __future__ import annotations
 
