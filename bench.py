@@ -640,8 +640,9 @@ def run_reference(a, wl, Q):
     X = W.clustered(n, wl.dim, wl.n_clusters, wl.sigma, wl.data_seed)[:n_s]
     import oracle
     R = oracle.gaussian(wl.r_seed, Q * wl.dim * wl.ell).reshape(Q, wl.dim, wl.ell)
+    # warm-up loads the oracle and touches its memory: a small slice will do
     for _ in range(a.warmup):
-        cpu_oracle_run(X, R, wl, n_s)
+        cpu_oracle_run(X, R, wl, min(n_s, 2000))
     t = 0.0
     for _ in range(a.steps):
         t += cpu_oracle_run(X, R, wl, n_s)
