@@ -200,6 +200,9 @@ CASES = [  # ell, k, d, Q, n, centres, flip
     (256, 9, 4, 1, 150, 8, 0.01),
     (33, 33, 3, 2, 200, 20, 0.05),
     (40, 5, 1, 2, 300, 40, 0.02),
+    (32, 4, 3, 2, 300, 10, 0.1),    # d = k - 1: one kept block per grouping
+    (64, 8, 4, 2, 2, 1, 0.0),       # two equal strings
+    (64, 8, 4, 1, 1, 1, 0.0),       # a single string: no pairs
 ]
 
 
