@@ -1,5 +1,6 @@
 """Host-side pieces of bench.py's roofline (no GPU): the word count of the
-pair check's ALU model and the algorithmic bytes of the HBM-bound kernels."""
+pair check's ALU model, the algorithmic bytes of the HBM-bound kernels, and
+the summary of the clock samples taken during the timed region."""
 import importlib.util
 import os
 
@@ -54,3 +55,20 @@ def test_algorithmic_bytes_hand_counts(bench):
     b, _, _ = bench.algorithmic("recheck", st, n, 128, 12, 2, 4)
     assert b == 1000 * (8 + 1024 + 12)
     assert bench.algorithmic("pair_check", st, n, 128, 12, 2, 4) == (None, None, None)
+
+
+def test_clock_samples_summary(bench):
+    # nvidia-smi --query-gpu=<ClockSampler.FIELDS> --format=csv,noheader,nounits
+    lines = [
+        "0, 2070, 2070, 674.97, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.2, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1201.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active",   # skipped
+        "truncated line",
+    ]
+    got = bench.parse_clocks(lines)
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 3,
+                   "reasons": ["sw_power_cap"]}
+    hot = ["0, 1500, 2070, 900, 0x48, Active, Active, Not Active, Not Active"]
+    assert bench.parse_clocks(hot)["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    assert bench.parse_clocks([]) is None
