@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--clocks-dir", default="",
                     help="folder for the raw nvidia-smi clock samples (default: temp dir)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", action="store_true",
+                    help="skip the all-cores copies of the CPU baseline")
     ap.add_argument("--no-missing", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-chunk", type=int, default=1 << 24,
@@ -639,6 +641,83 @@ def cpu_oracle_run(X, R, wl, n_s):
     return time.perf_counter() - t0
 
 
+_COPY = """
+import sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+import oracle
+X = np.load({x!r})
+R = np.load({r!r})
+oracle.lib()
+print("ready", flush=True)
+sys.stdin.readline()
+t0 = time.perf_counter()
+oracle.eps_graph(X, R, {ell}, {k}, {d}, oracle.COSINE, {eps!r})
+print(time.perf_counter() - t0, flush=True)
+"""
+
+
+def usable_cores():
+    """CPUs this process may run on: its affinity set, capped by a cgroup
+    CPU quota when one is set."""
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    try:
+        with open("/sys/fs/cgroup/cpu.max") as f:
+            quota, period = f.read().split()[:2]
+        if quota != "max":
+            n = min(n, max(1, int(-(-int(quota) // int(period)))))
+    except (OSError, ValueError):
+        pass
+    return max(1, n)
+
+
+def cpu_oracle_copies(X, R, wl, n_s, copies, timeout_s=240.0):
+    """The unchanged single-threaded oracle run as `copies` independent
+    processes on the same sample, released together once all have loaded:
+    returns (wall seconds, per-copy seconds), or None if any copy fails or
+    the run exceeds timeout_s (the copies are then killed)."""
+    import select
+    import tempfile
+
+    import oracle
+    oracle.build()          # the copies only load the shared object
+    with tempfile.TemporaryDirectory() as td:
+        xp, rp = os.path.join(td, "x.npy"), os.path.join(td, "r.npy")
+        np.save(xp, np.ascontiguousarray(X[:n_s]))
+        np.save(rp, np.ascontiguousarray(R))
+        code = _COPY.format(root=ROOT, x=xp, r=rp, ell=wl.ell, k=wl.k, d=wl.d,
+                            eps=float(wl.eps))
+        procs = [subprocess.Popen([sys.executable, "-c", code], stdin=subprocess.PIPE,
+                                  stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 for _ in range(copies)]
+        try:
+            deadline = time.monotonic() + timeout_s
+            for p in procs:
+                left = deadline - time.monotonic()
+                if left <= 0 or not select.select([p.stdout], [], [], left)[0]:
+                    return None
+                if p.stdout.readline().strip() != "ready":
+                    return None
+            t0 = time.perf_counter()
+            for p in procs:
+                p.stdin.write("go\n")
+                p.stdin.flush()
+            per = []
+            for p in procs:
+                out, _ = p.communicate(timeout=max(1.0, deadline - time.monotonic()))
+                if p.returncode != 0:
+                    return None
+                per.append(float(out.strip().splitlines()[-1]))
+            return time.perf_counter() - t0, per
+        except (subprocess.TimeoutExpired, ValueError, OSError):
+            return None
+        finally:
+            for p in procs:
+                if p.poll() is None:
+                    p.kill()
+                    p.wait()
+
+
 def run_reference(a, wl, Q):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -900,6 +979,21 @@ def main():
         cpu = {"value": n_s / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {n_s:,} of the {n:,} points, same R and Q={Q}; "
                          f"single-threaded C oracle, {t:.1f} s"}
+        # the same run on every core of the host: independent copies
+        cores = usable_cores()
+        allc = None
+        if cores > 1 and not a.no_cpu_all_cores:
+            try:
+                res = cpu_oracle_copies(Xh, R, wl, n_s, cores)
+            except Exception:  # noqa: BLE001 - a host-side measurement aid
+                res = None
+            if res:
+                wall, per = res
+                allc = {"value": cores * n_s / wall, "unit": UNIT, "cores": cores,
+                        "sample": f"{cores} concurrent copies of the same single-threaded "
+                                  f"{n_s:,}-point run; wall {wall:.1f} s, per copy "
+                                  f"{min(per):.1f}-{max(per):.1f} s"}
+        cpu["all_cores"] = allc
 
     if rank == 0:
         out = {

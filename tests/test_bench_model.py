@@ -72,3 +72,18 @@ def test_clock_samples_summary(bench):
     hot = ["0, 1500, 2070, 900, 0x48, Active, Active, Not Active, Not Active"]
     assert bench.parse_clocks(hot)["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
     assert bench.parse_clocks([]) is None
+
+
+def test_cpu_oracle_copies_run_and_time_out(bench):
+    import workloads as W
+    import oracle
+    wl = W.WORKLOADS["scale"]
+    X = W.clustered(600, 128, 30, 0.05, 1002)
+    R = oracle.gaussian(2002, 2 * 128 * 128).reshape(2, 128, 128)
+    res = bench.cpu_oracle_copies(X, R, wl, 600, 2)
+    assert res is not None
+    wall, per = res
+    assert len(per) == 2 and all(0 < p <= wall for p in per)
+    # an impossible deadline: no result, and the copies are killed
+    assert bench.cpu_oracle_copies(X, R, wl, 600, 2, timeout_s=1e-3) is None
+    assert bench.usable_cores() >= 1
