@@ -77,3 +77,44 @@ def test_first_adam_step_is_signed_lr():
     # m_hat / sqrt(v_hat) = g / |g| on the first step
     assert np.allclose(w2, w - 0.01 * np.array([1.0, -1.0, 0.0]), atol=1e-6)
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_adam_three_steps_hand_worked():
+    """Three Adam steps with carried moments, worked by hand (Kingma & Ba
+    2015, Algorithm 1) with beta1 = 1/2, beta2 = 3/4, eps = 0, lr = 1 and
+    gradients 1, -1, 2 from w = 0, m = v = 0:
+      t = 1: m = 1/2,     v = 1/4;           m^ = 1,    v^ = 1     -> w = -1
+      t = 2: m = 1/4 - 1/2 = -1/4,  v = 3/16 + 1/4 = 7/16;
+             m^ = (-1/4) / (3/4) = -1/3, v^ = (7/16) / (7/16) = 1  -> w = -2/3
+      t = 3: m = -1/8 + 1 = 7/8,  v = 21/64 + 1 = 85/64;
+             m^ = (7/8) / (7/8) = 1, v^ = (85/64) / (37/64) = 85/37
+                                                   -> w = -2/3 - sqrt(37/85)
+    Steps 2 and 3 start from nonzero moments, so a dropped beta1 * m or
+    beta2 * v term, or a missing bias correction, changes w."""
+    w, m, v = np.zeros(1), np.zeros(1), np.zeros(1)
+    want_w = [-1.0, -2.0 / 3.0, -2.0 / 3.0 - math.sqrt(37.0 / 85.0)]
+    want_m = [0.5, -0.25, 0.875]
+    want_v = [0.25, 7.0 / 16.0, 85.0 / 64.0]
+    for t, g in enumerate([1.0, -1.0, 2.0], start=1):
+        w, m, v = mlp.adam_step(w, np.array([g]), m, v, t, 1.0, beta1=0.5, beta2=0.75, eps=0.0)
+        assert w[0] == pytest.approx(want_w[t - 1], rel=1e-14, abs=1e-15)
+        assert m[0] == pytest.approx(want_m[t - 1], rel=1e-14)
+        assert v[0] == pytest.approx(want_v[t - 1], rel=1e-14)
+
+
+def test_adam_matches_torch_optimizer_float64():
+    """Five steps against torch.optim.Adam (an independent implementation)
+    in float64 with varying gradients; the oracle carries m and v between
+    calls exactly as the optimizer's state does."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    w0 = rng.normal(size=17)
+    grads = [rng.normal(size=17) * s for s in (1.0, 0.3, 2.0, 0.01, 5.0)]
+    p = torch.nn.Parameter(torch.tensor(w0, dtype=torch.float64))
+    opt = torch.optim.Adam([p], lr=0.05, betas=(0.8, 0.95), eps=1e-6)
+    w, m, v = w0.copy(), np.zeros(17), np.zeros(17)
+    for t, g in enumerate(grads, start=1):
+        p.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        w, m, v = mlp.adam_step(w, g, m, v, t, 0.05, beta1=0.8, beta2=0.95, eps=1e-6)
+        assert np.allclose(w, p.detach().numpy(), rtol=1e-13, atol=1e-15)
