@@ -529,16 +529,20 @@ def parse_clocks(lines):
         if len(p) < 9:
             continue
         try:
-            sm.append(float(p[1]))
-            mx.append(float(p[2]))
+            a = float(p[1])
         except ValueError:
             continue
+        sm.append(a)
+        try:
+            mx.append(float(p[2]))
+        except ValueError:
+            pass
         for nm, v in zip(names, p[5:9]):
             if v.lower().startswith("active"):
                 reasons.add(nm)
     if not sm:
         return None
-    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx) if mx else max(sm)),
             "samples": len(sm), "reasons": sorted(reasons)}
 
 

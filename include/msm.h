@@ -274,7 +274,10 @@ int msm_enumerate(const uint64_t* strings, int64_t n, int ell, int k, int d,
  * Every decision equals the one made on the double-precision distance of
  * Eq. 2 (cosine) or the Euclidean norm, accumulated by sequential fma;
  * returned distances are within 1e-5 relative of that value.  Output order
- * is unspecified.  MSM_E_ZERO_NORM for a zero row under MSM_COSINE. */
+ * is unspecified.  MSM_E_ZERO_NORM for a zero row under MSM_COSINE.
+ * MSM_E_INVAL when some candidate is not a pair i < j < n: such a candidate
+ * is skipped without reading X, and the outputs of that call are then
+ * incomplete. */
 int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
                 float eps, const uint64_t* cand, int64_t m,
                 uint64_t* pairs_out, float* dist_out, int64_t* count,
@@ -286,8 +289,9 @@ int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
  * process whose caching allocator has reserved the device, or a component
  * held to a fixed memory budget), where a cudaMalloc issued from this
  * library would fail or bypass the host's accounting.
- *   Arguments, outputs and results are those of msm_recheck; the caller
- *   still provides X, cand, pairs_out, dist_out and count.
+ *   Arguments, outputs, results and error codes are those of msm_recheck
+ *   (including MSM_E_INVAL for a candidate that is not a pair i < j < n);
+ *   the caller still provides X, cand, pairs_out, dist_out and count.
  *   Scratch: a static device array of about 3 MB per GPU that loads the
  *   library (row norms and counters), so n must be <= 262144 (2^18) rows;
  *   larger n returns MSM_E_INVAL with a message.  No cudaMalloc, cudaFree or

@@ -643,7 +643,7 @@ static int estimate_output(Scratch& sc, const void* Xd, int dtype, int64_t n, in
   int rc = launch_random_pairs(seed, samples, n, pr, s);
   if (rc) return rc;
   rc = launch_recheck(Xd, dtype, n, dim, metric, eps, n32, pr, nullptr, samples, nullptr,
-                      nullptr, cnt, cnt + 1, s);
+                      nullptr, cnt, cnt + 1, nullptr, s);
   if (rc) return rc;
   unsigned long long c = 0;
   rc = read_back(&c, cnt, s);
@@ -943,11 +943,12 @@ int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
   if (!ctr) return MSM_E_NOMEM;
   MSM_CUDA(cudaMemsetAsync(ctr, 0, 256, s));
   rc = launch_recheck(X, dtype, n, dim, metric, eps, n32, cand, nullptr, m,
-                      pairs_out, dist_out, ctr, ctr + 1, s);
+                      pairs_out, dist_out, ctr, ctr + 1, (unsigned*)(ctr + 2), s);
   if (rc) return rc;
-  unsigned long long h[2] = {0, 0};
+  unsigned long long h[3] = {0, 0, 0};
   MSM_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
   MSM_CUDA(cudaStreamSynchronize(s));
+  if (h[2]) return set_error("a candidate is not a pair i < j < n"), MSM_E_INVAL;
   *count = (int64_t)h[0];
   if (recomputed) *recomputed = (int64_t)h[1];
   return MSM_OK;
@@ -1148,7 +1149,7 @@ static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, i
   }
   tm.mark(5);
   rc = launch_recheck(Xd, dtype, n, dim, metric, eps, n32, cand, nullptr, m,
-                      pairs, dist, ctr, ctr + 1, s);
+                      pairs, dist, ctr, ctr + 1, nullptr, s);
   if (rc) return rc;
   unsigned long long h[3] = {0, 0, 0};
   MSM_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));

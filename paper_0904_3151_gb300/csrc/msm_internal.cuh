@@ -276,13 +276,15 @@ int mlp_adam(float* params, const float* grads, float* m, float* v, int64_t coun
              int step, float lr, float beta1, float beta2, float eps, void* w1h, void* w2h,
              int hidden, int dim, int dim_out, cudaStream_t s);
 
-// recheck.cu
+// recheck.cu.  bad_dev (optional): set nonzero when some candidate is not a
+// pair i < j < n (such candidates are skipped without reading X).
 int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
                    float eps, const float* nrm32, const uint64_t* cand,
                    const unsigned long long* m_dev, int64_t m_max,
                    uint64_t* pairs_out, float* dist_out,
                    unsigned long long* count_dev,
-                   unsigned long long* recompute_dev, cudaStream_t s);
+                   unsigned long long* recompute_dev, unsigned* bad_dev,
+                   cudaStream_t s);
 int launch_eps_count(const void* X, int dtype, int64_t n, int dim, int metric,
                      float eps, const float* nrm32,
                      unsigned long long* count_dev, cudaStream_t s);

@@ -21,13 +21,14 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 // L2 once and then hit in L1 for the rest of its pairs.  Kept pairs are
 // staged per warp in shared memory and appended kStage at a time: one
 // atomic on the output counter per 8 pairs serialised the whole kernel on
-// that one address.
+// that one address.  A candidate that is not a pair i < j < n is never read:
+// it is skipped and reported in *bad (when given).
 __global__ void __launch_bounds__(kThreads)
 recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
                float eps, const float* nrm, const uint64_t* cand,
                const unsigned long long* m_dev, int64_t m_max,
                uint64_t* pairs_out, float* dist_out, unsigned long long* count,
-               unsigned long long* recompute, float relS) {
+               unsigned long long* recompute, unsigned* bad, float relS) {
   constexpr int G = 4;  // lanes per pair: 8 pairs per warp in flight
   __shared__ uint64_t st_p[kThreads / 32][kStage];
   __shared__ float st_d[kThreads / 32][kStage];
@@ -54,9 +55,11 @@ recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
   unsigned long long nre = 0;
   for (int64_t base = c0 + (threadIdx.x >> 5) * (32 / G); base < c1; base += kPerIter) {
     const int64_t t = base + grp;
-    const bool valid = t < c1;
-    const uint64_t pr = valid ? cand[t] : 0;
+    const bool in_range = t < c1;
+    const uint64_t pr = in_range ? cand[t] : 0;
     const int64_t i = (int64_t)(pr >> 32), j = (int64_t)(pr & 0xffffffffu);
+    const bool valid = in_range && i < j && j < n;
+    if (in_range && !valid && sl == 0 && bad) atomicOr(bad, 1u);
     const float S = group_sq_dist<G>(X, dtype, valid ? i : 0, valid ? j : 0, dim, sl);
     bool keep = false, exact = false;
     double delta = 0.0;
@@ -155,7 +158,8 @@ int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
                    const unsigned long long* m_dev, int64_t m_max,
                    uint64_t* pairs_out, float* dist_out,
                    unsigned long long* count_dev,
-                   unsigned long long* recompute_dev, cudaStream_t s) {
+                   unsigned long long* recompute_dev, unsigned* bad_dev,
+                   cudaStream_t s) {
   if (m_max <= 0) return MSM_OK;
   const int64_t warps = (m_max + 7) / 8;
   int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
@@ -165,7 +169,7 @@ int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
   kt_begin(KC_RECHECK, s);
   recheck_kernel<<<(int)grid, kThreads, 0, s>>>(X, dtype, n, dim, metric, eps, nrm, cand,
                                                 m_dev, m_max, pairs_out, dist_out,
-                                                count_dev, recompute_dev, relS);
+                                                count_dev, recompute_dev, bad_dev, relS);
   kt_end(s);
   MSM_LAUNCH("recheck_kernel");
   return MSM_OK;

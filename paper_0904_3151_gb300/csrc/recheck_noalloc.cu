@@ -83,11 +83,12 @@ extern "C" int msm_recheck_noalloc(const void* X, int64_t n, int dim, int dtype,
   if ((f & 1u) && metric == MSM_COSINE)
     return set_error("cosine distance is undefined for an all-zero row"), MSM_E_ZERO_NORM;
   rc = launch_recheck(X, dtype, n, dim, metric, eps, n32, cand, nullptr, m,
-                      pairs_out, dist_out, ctr, ctr + 1, s);
+                      pairs_out, dist_out, ctr, ctr + 1, (unsigned*)(ctr + 2), s);
   if (rc) return rc;
-  unsigned long long h[2] = {0, 0};
+  unsigned long long h[3] = {0, 0, 0};
   MSM_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
   MSM_CUDA(cudaStreamSynchronize(s));
+  if (h[2]) return set_error("a candidate is not a pair i < j < n"), MSM_E_INVAL;
   *count = (int64_t)h[0];
   if (recomputed) *recomputed = (int64_t)h[1];
   return MSM_OK;

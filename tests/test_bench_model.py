@@ -72,6 +72,13 @@ def test_clock_samples_summary(bench):
     hot = ["0, 1500, 2070, 900, 0x48, Active, Active, Not Active, Not Active"]
     assert bench.parse_clocks(hot)["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
     assert bench.parse_clocks([]) is None
+    # an unreadable max clock: the SM sample still counts, and with no
+    # readable max at all the maximum falls back to the highest SM sample
+    na = ["0, 1900, [N/A], 800, 0x0, Not Active, Not Active, Not Active, Not Active",
+          "0, 2010, [N/A], 800, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    assert bench.parse_clocks(na) == {"sm_mhz": 1955.0, "sm_max_mhz": 2010.0, "samples": 2,
+                                      "reasons": []}
+    assert bench.parse_clocks(na + lines[:1])["sm_max_mhz"] == 2070.0
 
 
 def test_cpu_oracle_copies_run_and_time_out(bench):

@@ -255,6 +255,21 @@ def test_recheck_exact_ties(msm):
     assert set(_u64(p).tolist()) == set(cand[oracle.dist(Xc, cand, COS) <= 1.0].tolist())
 
 
+@pytest.mark.parametrize("bad", [(7, 300), (9, 9), (12, 5), (1 << 31, 2)])
+def test_recheck_rejects_out_of_range_pairs(msm, bad):
+    """A candidate that is not i < j < n (j = n, i = j, i > j, huge i) is
+    never read: the call returns MSM_E_INVAL, and the next call is clean."""
+    n, dim = 300, 16
+    X = W.clustered(n, dim, 4, 0.05, 3)
+    good = _pairs_from(np.arange(0, 40), np.arange(1, 41))
+    cand = np.append(good, np.uint64((bad[0] << 32) | bad[1]))
+    with pytest.raises(msm.MSMError) as e:
+        msm.recheck(_t(X), _t(cand.view(np.int64)), COS, 0.5)
+    assert e.value.status == -1 and "i < j < n" in str(e.value)
+    p, _, _ = msm.recheck(_t(X), _t(good.view(np.int64)), COS, 0.5)
+    assert np.array_equal(np.sort(_u64(p)), good[oracle.dist(X, good, COS) <= 0.5])
+
+
 # ------------------------------------------------------------ whole path
 
 def _eps_graph_case(msm, wl, Q, n=None, dtype="f32", **kw):
