@@ -1013,7 +1013,7 @@ def main():
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
             "roofline": roof, "hbm_kernels": hbm_kernels,
             "kernel_ms_per_step": {k: v / a.steps for k, v in kms.items()},
-            "stats": {k: st[k] for k in ("Q", "masks", "checks", "cand", "type1",
+            "stats": {k: st[k] for k in ("Q", "masks", "checks", "evaluated", "cand", "type1",
                                          "proj_recompute", "dist_recompute", "overflow_retries")},
             "missing_edges": missing, "forms": forms, "cpu_baseline": cpu,
         }

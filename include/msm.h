@@ -108,6 +108,10 @@ typedef struct msm_stats {
    * was 0) and that rule's output-size estimate S (-1 when not estimated). */
   int ell, k, d, reserved;
   double S_est;
+  /* In-group pairs that took the per-pair tests of the pair check: the
+   * pairs left by its tile-level reference prefilter (a subset of
+   * `checks`; the rest were decided a tile or a row at a time). */
+  int64_t evaluated;
 } msm_stats;
 
 /* Parameters of msm_eps_graph. */

@@ -34,7 +34,8 @@ class Stats(ctypes.Structure):
                 ("overflow_retries", ctypes.c_int64), ("ms", ctypes.c_float * 8),
                 ("kernel_ms", ctypes.c_float * 8), ("kernel_launches", ctypes.c_int64 * 8),
                 ("ell", ctypes.c_int), ("k", ctypes.c_int), ("d", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("S_est", ctypes.c_double)]
+                ("reserved", ctypes.c_int), ("S_est", ctypes.c_double),
+                ("evaluated", ctypes.c_int64)]
 
     PHASES = ["norms_R", "project", "group_sort", "group_bounds", "group_check",
               "recheck", "canonical", "total"]

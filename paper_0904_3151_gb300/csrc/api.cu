@@ -429,6 +429,7 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
   if (counters_out) *counters_out = counters;
   unsigned long long* count_dev = counters;
   unsigned long long* checks_dev = counters + 1;
+  unsigned long long* eval_dev = counters + 2;
 
   // Field layout of every pool for the in-group checks, when the blocks fit.
   const int FP = field_words(ell, k, sw);
@@ -493,6 +494,7 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
       pb.set_kept = fz.set_kept;
       pb.set_off = sets.off;
       pb.nsets = sets.S;
+      pb.evaluated = eval_dev;
       pb.ctas_per_sm = tu.check_ctas_per_sm;
       pb.min_blocks = tu.check_min_blocks;
       tm.mark(3);
@@ -542,9 +544,11 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
     total_cand = (int64_t)c;
   }
   if (st) {
-    unsigned long long ch = 0;
+    unsigned long long ch = 0, ev = 0;
     int rc = read_back(&ch, checks_dev, s);
+    if (!rc) rc = read_back(&ev, eval_dev, s);
     if (rc) return rc;
+    st->evaluated = (int64_t)ev;
     st->Q = Q;
     st->ell = ell;
     st->k = k;

@@ -1,13 +1,23 @@
 // Steps A3-A4: for every kept block set K of a batch, order the n strings of
 // one replicate so that strings with equal K blocks are adjacent (Sec. 2.1,
 // Fig. 1; Appendix, second trick: only grouping is needed, not a total
-// order).  One segment of n items per K; all segments sorted together by an
-// LSD radix sort with 8-bit digits, shared-memory histograms and warp-level
-// ranking.  The grouping key is computed from the strings inside the first
-// pass and never stored unsorted.
+// order).  One segment of n items per K; all segments are sorted together.
+// The grouping key is computed from the strings inside the first pass and
+// never stored unsorted.
+//
+// One point set: a most-significant-digit pass (shared-memory histograms,
+// one exclusive scan, stable scatter with warp-level ranking) splits every
+// segment into 256 buckets by the top 8 key bits, then one CTA per bucket
+// sorts it by the remaining bits in shared memory (three 8-bit LSD passes
+// between registers and shared memory) and writes it back in place: one
+// write and one read-modify-write of the items in HBM instead of four full
+// LSD passes.  Buckets larger than shared memory are sorted by the same CTA
+// in chunks through a scratch copy.  Several point sets: an LSD radix sort
+// with 8-bit digits whose tiles never straddle a set.
 //
 // Grouping key of string s under K (kept_bits = bits in the K blocks):
-//   kept_bits <= group_bits: the K blocks concatenated (exact);
+//   kept_bits <= group_bits: the K blocks concatenated (exact), passed
+//   through a bijection so that the top bits spread evenly;
 //   otherwise: the top group_bits bits of a 64-bit mix of the masked words.
 // Unequal K blocks may then share a key; the in-group check rejects such
 // pairs, since it requires the K blocks to be equal.
@@ -70,6 +80,17 @@ __device__ void setup_kept(KeptList& kl, const MaskDesc& md,
   }
 }
 
+// A bijection of the b-bit integers (odd multiply, xor-shift, odd multiply,
+// all modulo 2^b): an exact K-block part keeps its equality classes, and its
+// top bits become evenly spread, as the most-significant-digit pass of the
+// grouping needs.
+__device__ __forceinline__ uint64_t mix_bits(uint64_t x, int b) {
+  const uint64_t mask = b >= 64 ? ~0ull : ((1ull << b) - 1ull);
+  x = (x * 0x9E3779B97F4A7C15ull) & mask;
+  x ^= x >> ((b + 1) / 2);
+  return (x * 0xC2B2AE3D27D4EB4Full) & mask;
+}
+
 __device__ __forceinline__ uint32_t group_key(const uint64_t* str, int W,
                                               const KeptList& kl,
                                               int group_bits) {
@@ -84,6 +105,7 @@ __device__ __forceinline__ uint32_t group_key(const uint64_t* str, int W,
       kpart |= extract_bits(s, kl.lo[c], kl.width[c]) << off;
       off += kl.width[c];
     }
+    kpart = mix_bits(kpart, kl.kbits);
   } else {
     uint64_t h = 0x9E3779B97F4A7C15ull;
 #pragma unroll
@@ -305,6 +327,194 @@ scatter_kernel(SortArgs a) {
   }
 }
 
+// ----------------------------------------------------------- bucket sort
+constexpr int kBT = 512;              // threads of the bucket sort
+constexpr int kBIpt = 16;             // items per thread
+constexpr int kBCap = kBT * kBIpt;    // items a bucket may hold to sort in place
+
+struct BucketArgs {
+  uint32_t* keys;            // items sorted by the top digit, sorted in place
+  uint32_t* vals;
+  uint32_t* tkeys;           // scratch of the same size (large buckets)
+  uint32_t* tvals;
+  const uint32_t* offsets;   // exclusive scan of the top-digit counters
+  int64_t n;                 // items per segment
+  int tiles;                 // top-digit tiles per segment
+  int S;                     // segments
+  int passes;                // 8-bit passes below the top digit
+};
+
+struct BucketSmem {
+  uint32_t ks[kBCap];
+  uint32_t vs[kBCap];
+  uint32_t wh[kBT / 32][kRadix];  // per-warp digit counts, then warp prefixes
+  uint32_t dstart[kRadix];        // digit starts in the sorted chunk
+  uint32_t run[kRadix];           // running digit offsets (chunked sort)
+  uint32_t tmp[32];
+};
+
+// Stable rank of the digit (key >> shift) & 0xFF of the first m items held
+// in the warp-blocked order e = warp * 32 IPT + r * 32 + lane: pos[r] gets
+// the item's place in the digit-sorted order, sm.dstart the digit starts and
+// sm.wh[w][d] the count of digit d in warps before w.  Ends synchronised.
+template <int IPT>
+__device__ __forceinline__ void bucket_rank(const uint32_t (&key)[IPT], int shift, int m,
+                                            uint32_t (&pos)[IPT], BucketSmem& sm) {
+  constexpr int PER_WARP = 32 * IPT;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int t = tid; t < (kBT / 32) * kRadix; t += kBT) (&sm.wh[0][0])[t] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const int e = warp * PER_WARP + r * 32 + lane;
+    const bool valid = e < m;
+    const uint32_t digit = valid ? (key[r] >> shift) & 0xFFu : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    const int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (valid && lane == leader) old = sm.wh[warp][digit];
+    old = __shfl_sync(0xffffffffu, old, leader);
+    if (valid && lane == leader) sm.wh[warp][digit] = old + __popc(peers);
+    __syncwarp();
+    pos[r] = old + __popc(peers & lt_mask);
+  }
+  __syncthreads();
+  uint32_t run = 0;  // thread tid < kRadix owns digit tid
+  if (tid < kRadix) {
+#pragma unroll
+    for (int w = 0; w < kBT / 32; ++w) {
+      const uint32_t c = sm.wh[w][tid];
+      sm.wh[w][tid] = run;
+      run += c;
+    }
+  }
+  const uint32_t ds = block_exclusive_scan(run, sm.tmp);
+  if (tid < kRadix) sm.dstart[tid] = ds;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const int e = warp * PER_WARP + r * 32 + lane;
+    if (e < m) {
+      const uint32_t digit = (key[r] >> shift) & 0xFFu;
+      pos[r] += sm.dstart[digit] + sm.wh[warp][digit];
+    }
+  }
+}
+
+// One CTA per (segment, top digit) bucket: sort its items by the bits below
+// the top digit (stable, so equal keys keep their point order).
+__global__ void __launch_bounds__(kBT, 2)
+bucket_sort_kernel(BucketArgs a) {
+  extern __shared__ __align__(16) unsigned char bucket_smem[];
+  BucketSmem& sm = *reinterpret_cast<BucketSmem*>(bucket_smem);
+  constexpr int PER_WARP = 32 * kBIpt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int seg = blockIdx.x / kRadix, digit = blockIdx.x % kRadix;
+  const int64_t cb = (int64_t)seg * kRadix * a.tiles + (int64_t)digit * a.tiles;
+  const int64_t start = a.offsets[cb];
+  const int64_t end = digit + 1 < kRadix ? (int64_t)a.offsets[cb + a.tiles]
+                                         : (int64_t)(seg + 1) * a.n;
+  const int64_t m = end - start;
+  if (m <= 1) return;
+  uint32_t key[kBIpt], val[kBIpt], pos[kBIpt];
+  if (m <= kBCap) {
+#pragma unroll
+    for (int r = 0; r < kBIpt; ++r) {
+      const int e = warp * PER_WARP + r * 32 + lane;
+      key[r] = 0;
+      val[r] = 0;
+      if (e < m) {
+        key[r] = a.keys[start + e];
+        val[r] = a.vals[start + e];
+      }
+    }
+    for (int p = 0; p < a.passes; ++p) {
+      bucket_rank<kBIpt>(key, 8 * p, (int)m, pos, sm);
+#pragma unroll
+      for (int r = 0; r < kBIpt; ++r) {
+        const int e = warp * PER_WARP + r * 32 + lane;
+        if (e < m) {
+          sm.ks[pos[r]] = key[r];
+          sm.vs[pos[r]] = val[r];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < kBIpt; ++r) {
+        const int e = warp * PER_WARP + r * 32 + lane;
+        if (e < m) {
+          key[r] = sm.ks[e];
+          val[r] = sm.vs[e];
+        }
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < m; e += kBT) {  // coalesced write-back
+      a.keys[start + e] = sm.ks[e];
+      a.vals[start + e] = sm.vs[e];
+    }
+    return;
+  }
+  // A bucket larger than shared memory: each pass ranks it kBCap items at a
+  // time and scatters them to the other buffer (digit offsets carried from
+  // chunk to chunk), alternating between the items and the scratch copy.
+  uint32_t *sk = a.keys + start, *sv = a.vals + start;
+  uint32_t *dk = a.tkeys + start, *dv = a.tvals + start;
+  for (int p = 0; p < a.passes; ++p) {
+    const int shift = 8 * p;
+    if (tid < kRadix) sm.run[tid] = 0;
+    __syncthreads();
+    for (int64_t e = tid; e < m; e += kBT) atomicAdd(&sm.run[(sk[e] >> shift) & 0xFFu], 1u);
+    __syncthreads();
+    const uint32_t c = tid < kRadix ? sm.run[tid] : 0u;
+    __syncthreads();
+    const uint32_t rs = block_exclusive_scan(c, sm.tmp);
+    if (tid < kRadix) sm.run[tid] = rs;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < m; c0 += kBCap) {
+      const int cm = (int)min((int64_t)kBCap, m - c0);
+#pragma unroll
+      for (int r = 0; r < kBIpt; ++r) {
+        const int e = warp * PER_WARP + r * 32 + lane;
+        key[r] = 0;
+        val[r] = 0;
+        if (e < cm) {
+          key[r] = sk[c0 + e];
+          val[r] = sv[c0 + e];
+        }
+      }
+      bucket_rank<kBIpt>(key, shift, cm, pos, sm);
+#pragma unroll
+      for (int r = 0; r < kBIpt; ++r) {
+        const int e = warp * PER_WARP + r * 32 + lane;
+        if (e < cm) {
+          const uint32_t d = (key[r] >> shift) & 0xFFu;
+          const uint32_t q = sm.run[d] + pos[r] - sm.dstart[d];
+          dk[q] = key[r];
+          dv[q] = val[r];
+        }
+      }
+      __syncthreads();
+      // this chunk's digit counts advance the running offsets
+      if (tid < kRadix) {
+        const uint32_t next = tid + 1 < kRadix ? sm.dstart[tid + 1] : (uint32_t)cm;
+        sm.run[tid] += next - sm.dstart[tid];
+      }
+      __syncthreads();
+    }
+    uint32_t* t;
+    t = sk; sk = dk; dk = t;
+    t = sv; sv = dv; dv = t;
+  }
+  if (sk != a.keys + start) {  // odd number of passes: copy back
+    for (int64_t e = tid; e < m; e += kBT) {
+      a.keys[start + e] = sk[e];
+      a.vals[start + e] = sv[e];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ scans
 constexpr int kScanChunk = kThreads * 16;
 
@@ -507,6 +717,44 @@ int run_grouping(const GroupBatch& b, void* ws, uint32_t** keys_out,
   a.set_off = b.sets.off;
   if (tiles == 0) return set_error("grouping: no radix tiles"), MSM_E_INVAL;
   dim3 grid(tiles, b.S);
+  if (!b.sets.tile_set && b.passes >= 2) {
+    // one point set: top-digit pass, then every bucket sorted in place
+    a.shift = b.group_bits - 8;
+    a.keys_in = nullptr;
+    a.vals_in = nullptr;
+    a.keys_out = kA;
+    a.vals_out = vA;
+    kt_begin(KC_HIST, s);
+    hist_kernel<uint32_t, true, kIpt32><<<grid, kThreads, 0, s>>>(a);
+    kt_end(s);
+    MSM_LAUNCH("hist_kernel");
+    int rc = exclusive_scan_u32(counts, offsets, ncounts, scan_ws, nullptr, s);
+    if (rc) return rc;
+    kt_begin(KC_SCATTER, s);
+    scatter_kernel<uint32_t, true, kIpt32><<<grid, kThreads, 0, s>>>(a);
+    kt_end(s);
+    MSM_LAUNCH("scatter_kernel");
+    BucketArgs ba;
+    ba.keys = kA;
+    ba.vals = vA;
+    ba.tkeys = kB;
+    ba.tvals = vB;
+    ba.offsets = offsets;
+    ba.n = b.n;
+    ba.tiles = tiles;
+    ba.S = b.S;
+    ba.passes = (b.group_bits - 8 + 7) / 8;
+    const size_t smem = sizeof(BucketSmem);
+    MSM_CUDA(cudaFuncSetAttribute(bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    kt_begin(KC_SCATTER, s);
+    bucket_sort_kernel<<<(unsigned)(b.S * kRadix), kBT, smem, s>>>(ba);
+    kt_end(s);
+    MSM_LAUNCH("bucket_sort_kernel");
+    *keys_out = kA;
+    *vals_out = vA;
+    return MSM_OK;
+  }
   uint32_t *ki = nullptr, *vi = nullptr, *ko = kA, *vo = vA;
   for (int pass = 0; pass < b.passes; ++pass) {
     a.shift = 8 * pass;

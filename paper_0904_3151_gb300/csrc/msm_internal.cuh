@@ -239,6 +239,8 @@ struct PairBatch {
   const int64_t* set_off = nullptr;      // device [nsets + 1]
   int nsets = 1;
   int sw = 1;                            // bits per symbol (1: sign bits)
+  unsigned long long* evaluated = nullptr;  // pairs that took the per-pair
+                                           // tests after the prefilter
   // launch tuning of the pair check (0 = defaults)
   int ctas_per_sm = 0;
   int min_blocks = 0;                    // fused variant: 2, 4 or 5

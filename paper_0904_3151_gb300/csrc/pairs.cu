@@ -226,6 +226,9 @@ __host__ __device__ __forceinline__ uint64_t tiles_of(uint64_t len) {
   return t * (t + 1) / 2;
 }
 
+// Work of every run (one item per run of at most 32 members, else one per
+// 32 x 32 tile of its upper triangle); also adds the in-group pairs to
+// *checks.
 __global__ void run_work_kernel(const uint32_t* starts, const uint32_t* ends,
                                 const uint32_t* ngroups, uint64_t* work,
                                 unsigned long long* checks) {
@@ -275,6 +278,7 @@ struct CheckArgs {
   const int64_t* set_off;
   int nsets;
   int sw;  // bits per symbol: Hamming distances count differing symbols
+  unsigned long long* evaluated;  // pairs that took the per-pair tests (or NULL)
 };
 
 // Number of differing symbols in x = a ^ b (symbols of sw = 1, 2 or 4 bits
@@ -731,43 +735,6 @@ __device__ __forceinline__ bool gaps_differ(const uint32_t (&fa)[FP],
   return bad == 0;
 }
 
-// Gap test of one tile row against the tile's columns, over the first NW
-// field words only (the words above the highest gap block hold no gap
-// field).  Diagonal tile: round robin -- in step s lane l pairs with column
-// (l + s) mod 32; steps 1..15 and the lower half of step 16 cover every
-// unordered pair of the block exactly once with all lanes busy.
-template <int FP, int NW>
-__device__ __forceinline__ uint32_t tile_gaps_n(bool diag, const uint32_t (&fa)[FP],
-                                                const uint32_t (*sf)[FP],
-                                                const uint32_t (&gapf)[FP], uint32_t ncols,
-                                                int lane) {
-  uint32_t gpass = 0;
-  if (diag) {
-#pragma unroll 4
-    for (int s = 1; s <= 16; ++s) {
-      const int c = (lane + s) & 31;
-      const bool ok = (s < 16 || lane < 16) && gaps_differ<FP, NW>(fa, sf[c], gapf);
-      gpass |= (uint32_t)ok << c;
-    }
-  } else {
-#pragma unroll 4
-    for (uint32_t c = 0; c < ncols; ++c)
-      gpass |= (uint32_t)gaps_differ<FP, NW>(fa, sf[c], gapf) << c;
-  }
-  return gpass;
-}
-
-template <int FP, int N>
-__device__ __forceinline__ uint32_t tile_gaps(int nw, bool diag, const uint32_t (&fa)[FP],
-                                              const uint32_t (*sf)[FP],
-                                              const uint32_t (&gapf)[FP], uint32_t ncols,
-                                              int lane) {
-  if constexpr (N > 0) {
-    if (nw < N) return tile_gaps<FP, N - 1>(nw, diag, fa, sf, gapf, ncols, lane);
-  }
-  return tile_gaps_n<FP, N>(diag, fa, sf, gapf, ncols, lane);
-}
-
 // Hamming (differing symbols) <= d and (hashed keys only) all kept fields
 // equal.
 template <int FP, int FU>
@@ -786,11 +753,12 @@ __device__ __forceinline__ bool fields_rest_ok(const uint32_t (&fa)[FP],
   return h <= d && (!hashed || bad == 0);
 }
 
+// No replicate g0 <= g < q has the pair within d (Appendix, first trick).
 template <int FP>
 __device__ __forceinline__ bool replicates_ok_fields(const CheckArgs& a,
                                                      const uint32_t* fields,
-                                                     uint32_t i, uint32_t j) {
-  for (int g = 0; g < a.q; ++g) {
+                                                     uint32_t i, uint32_t j, int g0 = 0) {
+  for (int g = g0; g < a.q; ++g) {
     const uint2* fi = reinterpret_cast<const uint2*>(fields + ((size_t)g * a.n + i) * FP);
     const uint2* fj = reinterpret_cast<const uint2*>(fields + ((size_t)g * a.n + j) * FP);
     int h = 0;
@@ -804,64 +772,164 @@ __device__ __forceinline__ bool replicates_ok_fields(const CheckArgs& a,
   return true;
 }
 
+template <int FP>
+__device__ __forceinline__ void load_fields(const uint32_t* pool, uint32_t idx,
+                                            uint32_t (&f)[FP]) {
+  const uint2* src = reinterpret_cast<const uint2*>(pool + (size_t)idx * FP);
+#pragma unroll
+  for (int w = 0; w < FP; w += 2) {
+    const uint2 v = src[w / 2];
+    f[w] = v.x;
+    f[w + 1] = v.y;
+  }
+}
+
+// ------------------------------------------------ pair check (field layout)
+// Work items: a run of more than 32 members is split into 32 x 32 tiles
+// (I, J), I <= J, of its upper triangle, enumerated column by column, so the
+// tiles of one column block J (a strip) are consecutive items; a run of at
+// most 32 members is the one diagonal tile (0, 0).  A warp takes chunks of
+// consecutive items and reads the metadata of 32 items at once, one per
+// lane (group, tile, and the sub-key skip below), so that the dependent
+// loads of consecutive items overlap.
+//
+// Each warp keeps the column block of its last tile in shared memory: the
+// members' fields, their replicate-0 fields and, for every gap block of the
+// grouping, a reference value and the mask of columns that carry it.  A
+// tile of the same strip only stages its rows.
+//
+// Reference prefilter: the reference of a gap block is its most frequent
+// value among the block's 32 columns.  A row and a column that both carry
+// it are equal on that gap block, which the first-mask rule rejects, so a
+// row drops every column at the reference of each gap block where the row
+// itself is at the reference -- one and-not per gap block per row instead
+// of a gap test per pair.  Any reference value gives the same result;
+// frequent ones drop the most pairs.  The remaining pairs are queued in
+// shared memory and take the exact tests 32 at a time, one pair per lane:
+// every gap block differs, Hamming <= d, kept blocks equal (hashed keys
+// only), and no earlier replicate within d (Appendix) -- replicate 0 from the
+// staged fields, later ones from global memory.  Passing pairs are compacted
+// to the front of the same queue (a round writes only entries already read)
+// and collected in a per-warp buffer that is appended to E with one atomic
+// when full, so the pairs of consecutive tiles lie together in E (the
+// recheck then finds their rows in L1).
+constexpr int kOut = 64;  // per-warp buffer of pairs for E
+
+template <int FP>
+struct WarpStage {
+  uint32_t cf[32][FP];   // column block: fields of this replicate
+  uint32_t cf0[32][FP];  // and of replicate 0
+  uint32_t ci[32];       // points
+  uint32_t rf[32][FP];   // rows of the current tile (off-diagonal)
+  uint32_t rf0[32][FP];
+  uint32_t ri[32];
+  uint32_t ref[kMaxFieldBlocks];    // reference value per gap block
+  uint32_t colat[kMaxFieldBlocks];  // columns at the reference
+  uint64_t out[kOut];               // pairs waiting to be appended to E
+};
+
+// Appends the warp's buffered pairs to E (one atomic).
+template <int FP>
+__device__ __forceinline__ void flush_out(const CheckArgs& a, WarpStage<FP>& ws, uint32_t& nout,
+                                          int lane) {
+  if (!nout) return;
+  __syncwarp();
+  unsigned long long b = 0;
+  if (lane == 0) b = atomicAdd(a.count, (unsigned long long)nout);
+  b = __shfl_sync(0xffffffffu, b, 0);
+  for (uint32_t t = lane; t < nout; t += 32)
+    if (b + t < (unsigned long long)a.cap) a.cand[b + t] = ws.out[t];
+  __syncwarp();
+  nout = 0;
+}
+
 template <int FP, int FU, bool FUSE, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
 check_fields_kernel(CheckArgs a, const uint32_t* fields) {
-  __shared__ __align__(16) uint32_t sm_f[kThreads / 32][32][FP];
-  __shared__ uint32_t sm_i[kThreads / 32][32];
+  __shared__ __align__(16) WarpStage<FP> stg[kThreads / 32];
   __shared__ uint64_t sm_q[kThreads / 32][32];       // fused recheck queue
-  __shared__ uint32_t sm_fr[kThreads / 32][32][FP];  // tile rows' fields
-  __shared__ uint32_t sm_ir[kThreads / 32][32];      // tile rows' points
-  __shared__ uint16_t sm_qs[kThreads / 32][1024];    // survivors: row << 5 | column
-  // pair p of a group of <= 32 items, column by column: p = b(b-1)/2 + a
-  __shared__ uint8_t tri_a[496], tri_b[496];
+  __shared__ uint16_t sm_qs[kThreads / 32][1024];    // queued pairs: row << 5 | column
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int p = threadIdx.x; p < 496; p += kThreads) {
-    int b = 1;
-    while ((b + 1) * b / 2 <= p) ++b;
-    tri_a[p] = (uint8_t)(p - b * (b - 1) / 2);
-    tri_b[p] = (uint8_t)b;
-  }
-  __syncthreads();
+  WarpStage<FP>& ws = stg[warp];
   const uint64_t total = *a.total_work;
   const uint32_t G = *a.ngroups;
   if (total == 0 || G == 0) return;
   const uint64_t C = chunk_size(total, a.chunk_cap);
   const uint64_t nch = (total + C - 1) / C;
   const uint32_t* pool = fields + (size_t)a.q * a.n * FP;
+  const uint32_t* pool0 = fields;  // replicate 0
+  const bool rep0 = a.q > 0;
   FuseAcc acc;
   uint32_t cur_g = 0xffffffffu;
-  int cur_seg = -1, subw = 0, nw = 0;
+  int cur_seg = -1;
+  uint32_t Gs = 0;  // gap blocks of the current grouping
   bool hashed = false;
   uint32_t gapf[FP], keepf[FP];
 #pragma unroll
   for (int w = 0; w < FP; ++w) gapf[w] = keepf[w] = 0;
-  for (;;) {  // dynamic chunks of work items (see check_kernel)
+  uint32_t cache_g = 0xffffffffu, cache_J = 0;  // column block held in ws
+  uint32_t nout = 0;                            // pairs in ws.out (warp-uniform)
+  unsigned long long evaluated = 0;             // queued pairs (warp-uniform)
+  for (;;) {  // dynamic chunks of work items
   unsigned chunk = 0;
   if (lane == 0) chunk = atomicAdd(a.grab, 1u);
   chunk = __shfl_sync(0xffffffffu, chunk, 0);
   if (chunk >= nch) break;
   const uint64_t w0 = (uint64_t)chunk * C, w1 = min(total, w0 + C);
-  uint32_t g = a.chunk_group[chunk];
-  for (uint64_t item = w0; item < w1; ++item) {
-    while (g + 1 < G && a.work_prefix[g + 1] <= item) ++g;
-    const uint64_t local = item - a.work_prefix[g];
-    const uint32_t st = a.starts[g];
-    const uint32_t len = a.ends[g] - st + 1;
-    const int seg = (int)(st / a.n);
-    if (FUSE && g != cur_g) {
-      cur_g = g;
-      fuse_enter(a, acc, a.vals[st], lane);
+  uint32_t gb = a.chunk_group[chunk];  // group of item w0
+  for (uint64_t base = w0; base < w1; base += 32) {
+    // metadata of items base .. base + 31, one per lane; every group holds
+    // at least one item, so they lie in groups gb .. gb + 31
+    const uint64_t item = base + lane;
+    const bool iv = item < w1;
+    const uint64_t wp = gb + lane < G ? a.work_prefix[gb + lane] : ~0ull;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) cnt += __shfl_sync(0xffffffffu, wp, i) <= item;
+    const uint32_t g = gb + cnt - 1;
+    const uint64_t local = item - __shfl_sync(0xffffffffu, wp, (int)((cnt - 1) & 31u));
+    gb = __shfl_sync(0xffffffffu, g, 31);
+    uint32_t st = 0, len = 0, I = 0, J = 0;
+    bool live = false;
+    if (iv) {
+      st = a.starts[g];
+      len = a.ends[g] - st + 1;
+      if (len > kSmall) {
+        uint64_t J64 = (uint64_t)((sqrtf(8.0f * (float)local + 1.0f) - 1.0f) * 0.5f);
+        while (J64 * (J64 + 1) / 2 > local) --J64;
+        while ((J64 + 1) * (J64 + 2) / 2 <= local) ++J64;
+        J = (uint32_t)J64;
+        I = (uint32_t)(local - J64 * (J64 + 1) / 2);
+      }
+      // every member of the tile in one run of equal full keys: all its
+      // pairs are equal on the first gap block, so none is reported here
+      live = true;
+      if (a.masks[st / a.n].sub_width) {
+        const uint32_t last = min(len - 1, J * 32 + 31);
+        live = a.keys[st + I * 32] != a.keys[st + last];
+      }
+    }
+    unsigned lv = __ballot_sync(0xffffffffu, live);
+    while (lv) {
+    const int t = __ffs(lv) - 1;
+    lv &= lv - 1;
+    const uint32_t tg = __shfl_sync(0xffffffffu, g, t);
+    const uint32_t tst = __shfl_sync(0xffffffffu, st, t);
+    const uint32_t tlen = __shfl_sync(0xffffffffu, len, t);
+    const uint32_t tI = __shfl_sync(0xffffffffu, I, t);
+    const uint32_t tJ = __shfl_sync(0xffffffffu, J, t);
+    const int seg = (int)(tst / a.n);
+    if (FUSE && tg != cur_g) {
+      cur_g = tg;
+      fuse_enter(a, acc, a.vals[tst], lane);
     }
     if (seg != cur_seg) {
       const MaskDesc& md = a.masks[seg];
       cur_seg = seg;
       hashed = md.hashed != 0;
-      subw = md.sub_width;
       // gap blocks: below the highest kept block and not kept
       const uint32_t K = md.K;
-      const uint32_t Gs = ((1u << md.maxK) - 1u) & ~K;
-      nw = Gs ? (31 - __clz(Gs)) / 2 + 1 : 0;  // words up to the highest gap block
+      Gs = ((1u << md.maxK) - 1u) & ~K;
 #pragma unroll
       for (int w = 0; w < FP; ++w) {
         gapf[w] = ((Gs >> (2 * w)) & 1u ? 0x8000u : 0u) |
@@ -870,177 +938,175 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
                    ((K >> (2 * w + 1)) & 1u ? 0x80000000u : 0u);
       }
     }
-    if (len <= kSmall) {
-      // all members equal on the first gap block: nothing to report here
-      if (subw && a.keys[st] == a.keys[st + len - 1]) continue;
-      if (lane < (int)len) {
-        const uint32_t idx = a.vals[st + lane];
-        sm_i[warp][lane] = idx;
-        const uint2* src = reinterpret_cast<const uint2*>(pool + (size_t)idx * FP);
+    const bool diag = tI == tJ;
+    const uint32_t ncols = min(32u, tlen - tJ * 32);
+    const bool pf = tlen > 8;  // tiny runs have too few pairs for the prefilter
+    __syncwarp();  // the previous item's queue stage is done with the stage
+    if (tg != cache_g || tJ != cache_J) {
+      // stage the column block, its references and masks
+      const uint32_t cb = tJ * 32 + lane;
+      const bool vc = cb < tlen;
+      uint32_t f[FP], f0[FP];
+      uint32_t ic = 0;
 #pragma unroll
-        for (int w = 0; w < FP; w += 2) {
-          const uint2 v = src[w / 2];
-          sm_f[warp][lane][w] = v.x;
-          sm_f[warp][lane][w + 1] = v.y;
-        }
+      for (int w = 0; w < FP; ++w) f[w] = f0[w] = 0;
+      if (vc) {
+        ic = a.vals[tst + cb];
+        load_fields<FP>(pool, ic, f);
+        if (rep0) load_fields<FP>(pool0, ic, f0);
       }
-      __syncwarp();
-      const int P = (int)(len * (len - 1) / 2);
-      uint32_t npass = 0;  // passing pairs, compacted into sm_qs (non-fused)
-      for (int r = 0; r < P; r += 32) {
-        const int p = r + lane;
-        bool pass = false;
-        uint32_t ii = 0, jj = 0;
-        if (p < P) {
-          const int aa = tri_a[p], b = tri_b[p];
-          uint32_t fa[FP];
 #pragma unroll
-          for (int w = 0; w < FP; ++w) fa[w] = sm_f[warp][aa][w];
-          if (gaps_differ<FP, FU>(fa, sm_f[warp][b], gapf) &&
-              fields_rest_ok<FP, FU>(fa, sm_f[warp][b], a.d, a.sw, hashed, keepf)) {
-            ii = sm_i[warp][aa];
-            jj = sm_i[warp][b];
-            pass = replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj, ii < jj ? jj : ii);
-          }
-        }
-        if constexpr (FUSE) {
-          fuse_one(a, pass, ii, jj, lane, sm_q[warp], acc);
-          continue;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, pass);
-        if (pass) sm_qs[warp][npass + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)p;
-        npass += __popc(bal);
+      for (int w = 0; w < FP; ++w) {
+        ws.cf[lane][w] = f[w];
+        ws.cf0[lane][w] = f0[w];
       }
-      if (!FUSE && npass) {
-        // one append per work item: its pairs lie together in E, so the
-        // recheck finds their (at most 32) rows in L1
-        __syncwarp();
-        unsigned long long b0 = 0;
-        if (lane == 0) b0 = atomicAdd(a.count, (unsigned long long)npass);
-        b0 = __shfl_sync(0xffffffffu, b0, 0);
-        for (uint32_t t = lane; t < npass; t += 32) {
-          const uint32_t p = sm_qs[warp][t];
-          const uint32_t ii = sm_i[warp][tri_a[p]], jj = sm_i[warp][tri_b[p]];
-          if (b0 + t < (unsigned long long)a.cap) a.cand[b0 + t] = ordered_pair(ii, jj);
-        }
-      }
-      __syncwarp();
-    } else {
-      uint64_t J = (uint64_t)((sqrtf(8.0f * (float)local + 1.0f) - 1.0f) * 0.5f);
-      while (J * (J + 1) / 2 > local) --J;
-      while ((J + 1) * (J + 2) / 2 <= local) ++J;
-      const uint64_t I = local - J * (J + 1) / 2;
-      // the whole tile inside one run of equal full keys: every pair is
-      // equal on the first gap block, so none is reported under this K
-      if (subw) {
-        const uint32_t last = (uint32_t)min((uint64_t)len - 1, J * 32 + 31);
-        if (a.keys[st + (uint32_t)(I * 32)] == a.keys[st + last]) continue;
-      }
-      const uint32_t ra = (uint32_t)(I * 32 + lane);
-      const bool va = ra < len;
-      uint32_t fa[FP];
-      uint32_t ia = 0;
+      ws.ci[lane] = ic;
+      if (pf) {
 #pragma unroll
-      for (int w = 0; w < FP; ++w) fa[w] = 0;
-      if (va) {
-        ia = a.vals[st + ra];
-        const uint2* src = reinterpret_cast<const uint2*>(pool + (size_t)ia * FP);
+        for (int w = 0; w < FU; ++w) {
 #pragma unroll
-        for (int w = 0; w < FP; w += 2) {
-          const uint2 v = src[w / 2];
-          fa[w] = v.x;
-          fa[w + 1] = v.y;
-        }
-      }
-      const uint32_t cb = (uint32_t)(J * 32 + lane);
-      if (cb < len) {
-        const uint32_t idx = a.vals[st + cb];
-        sm_i[warp][lane] = idx;
-        const uint2* src = reinterpret_cast<const uint2*>(pool + (size_t)idx * FP);
-#pragma unroll
-        for (int w = 0; w < FP; w += 2) {
-          const uint2 v = src[w / 2];
-          sm_f[warp][lane][w] = v.x;
-          sm_f[warp][lane][w + 1] = v.y;
-        }
-      }
-      __syncwarp();
-      const uint32_t ncols = min(32u, len - (uint32_t)(J * 32));
-      const uint32_t colmask = ncols == 32 ? 0xffffffffu : ((1u << ncols) - 1u);
-      uint32_t gpass = tile_gaps<FP, FU>(nw, I == J, fa, sm_f[warp], gapf, ncols, lane);
-      gpass &= va ? colmask : 0u;
-      // Survivors of the gap test (~5 % of the pairs) take the Hamming, kept-
-      // block and replicate tests.  The replicate test reads earlier pools
-      // from global memory, so the survivors of the whole tile are queued
-      // once in shared memory and tested 32 at a time, one per lane: the
-      // loads of 32 pairs are in flight together instead of each lane
-      // walking its own survivors one dependent load after another.  The
-      // passing pairs are compacted to the front of the same queue (a round
-      // writes only entries already read) and the tile appends them to E
-      // with one atomic, so they lie together there: the recheck then finds
-      // the tile's (at most 64) rows in L1.
-      uint32_t cnt = __popc(gpass), incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      if (total) {
-#pragma unroll
-        for (int w = 0; w < FP; ++w) sm_fr[warp][lane][w] = fa[w];
-        sm_ir[warp][lane] = ia;
-        uint32_t npass = 0;
-        uint32_t m = gpass, pos = incl - cnt;
-        while (m) {
-          const int c = __ffs(m) - 1;
-          m &= m - 1;
-          sm_qs[warp][pos++] = (uint16_t)(((uint32_t)lane << 5) | c);
-        }
-        for (uint32_t b0 = 0; b0 < total; b0 += 32) {
-          __syncwarp();
-          const uint32_t nb = min(32u, total - b0);
-          bool ok = false;
-          uint32_t ii = 0, jj = 0, r = 0, c = 0;
-          if ((uint32_t)lane < nb) {
-            const uint32_t e = sm_qs[warp][b0 + lane];
-            r = e >> 5;
-            c = e & 31u;
-            uint32_t fr[FP];
-#pragma unroll
-            for (int w = 0; w < FP; ++w) fr[w] = sm_fr[warp][r][w];
-            if (fields_rest_ok<FP, FU>(fr, sm_f[warp][c], a.d, a.sw, hashed, keepf)) {
-              ii = sm_ir[warp][r];
-              jj = sm_i[warp][c];
-              ok = replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj, ii < jj ? jj : ii);
+          for (int h = 0; h < 2; ++h) {
+            const int b = 2 * w + h;
+            if (!((Gs >> b) & 1u)) continue;  // warp-uniform
+            // columns outside the block carry a value no field can hold
+            const uint32_t v =
+                vc ? (f[w] >> (16 * h)) & 0x7FFFu : (0x10000u | (uint32_t)lane);
+            const uint32_t peers = __match_any_sync(0xffffffffu, v);
+            const uint32_t best = __reduce_max_sync(
+                0xffffffffu, ((uint32_t)__popc(peers) << 5) | (uint32_t)lane);
+            const uint32_t ref = __shfl_sync(0xffffffffu, v, (int)(best & 31u));
+            const uint32_t at = __ballot_sync(0xffffffffu, v == ref);
+            if (lane == 0) {
+              ws.ref[b] = ref;
+              ws.colat[b] = at;
             }
           }
-          if constexpr (FUSE) {
-            fuse_one(a, ok, ii, jj, lane, sm_q[warp], acc);
-          } else {
-            const unsigned bal = __ballot_sync(0xffffffffu, ok);
-            __syncwarp();
-            if (ok) sm_qs[warp][npass + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((r << 5) | c);
-            npass += __popc(bal);
-          }
         }
-        if (!FUSE && npass) {
-          __syncwarp();
-          unsigned long long b1 = 0;
-          if (lane == 0) b1 = atomicAdd(a.count, (unsigned long long)npass);
-          b1 = __shfl_sync(0xffffffffu, b1, 0);
-          for (uint32_t t = lane; t < npass; t += 32) {
-            const uint32_t e = sm_qs[warp][t];
-            const uint32_t ii = sm_ir[warp][e >> 5], jj = sm_i[warp][e & 31u];
-            if (b1 + t < (unsigned long long)a.cap) a.cand[b1 + t] = ordered_pair(ii, jj);
+      }
+      cache_g = tg;
+      cache_J = tJ;
+      __syncwarp();
+    }
+    // rows: the column block itself on the diagonal, else staged here
+    const uint32_t ra = tI * 32 + lane;
+    const bool va = ra < tlen;
+    uint32_t fa[FP];
+    if (diag) {
+#pragma unroll
+      for (int w = 0; w < FP; ++w) fa[w] = ws.cf[lane][w];
+    } else {
+      uint32_t f0[FP];
+      uint32_t ia = 0;
+#pragma unroll
+      for (int w = 0; w < FP; ++w) fa[w] = f0[w] = 0;
+      if (va) {
+        ia = a.vals[tst + ra];
+        load_fields<FP>(pool, ia, fa);
+        if (rep0) load_fields<FP>(pool0, ia, f0);
+      }
+#pragma unroll
+      for (int w = 0; w < FP; ++w) {
+        ws.rf[lane][w] = fa[w];
+        ws.rf0[lane][w] = f0[w];
+      }
+      ws.ri[lane] = ia;
+    }
+    uint32_t cand = va ? (ncols == 32 ? 0xffffffffu : ((1u << ncols) - 1u)) : 0u;
+    if (diag) cand &= lane == 31 ? 0u : (0xffffffffu << (lane + 1));
+    if (pf) {
+#pragma unroll
+      for (int w = 0; w < FU; ++w) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int b = 2 * w + h;
+          if (((Gs >> b) & 1u) && ((fa[w] >> (16 * h)) & 0x7FFFu) == ws.ref[b])
+            cand &= ~ws.colat[b];
+        }
+      }
+    }
+    const uint32_t cnt2 = __popc(cand);
+    uint32_t incl = cnt2;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t nq = __shfl_sync(0xffffffffu, incl, 31);
+    if (nq == 0) continue;
+    {
+      uint32_t m = cand, pos = incl - cnt2;
+      while (m) {
+        const int c = __ffs(m) - 1;
+        m &= m - 1;
+        sm_qs[warp][pos++] = (uint16_t)(((uint32_t)lane << 5) | (uint32_t)c);
+      }
+    }
+    __syncwarp();
+    evaluated += nq;
+    const uint32_t (*rowf)[FP] = diag ? ws.cf : ws.rf;
+    const uint32_t (*rowf0)[FP] = diag ? ws.cf0 : ws.rf0;
+    const uint32_t* rowi = diag ? ws.ci : ws.ri;
+    uint32_t npass = 0;
+    for (uint32_t b0 = 0; b0 < nq; b0 += 32) {
+      __syncwarp();
+      const uint32_t nb = min(32u, nq - b0);
+      bool ok = false;
+      uint32_t ii = 0, jj = 0, e = 0;
+      if ((uint32_t)lane < nb) {
+        e = sm_qs[warp][b0 + lane];
+        const uint32_t r = e >> 5, c = e & 31u;
+        uint32_t fr[FP];
+#pragma unroll
+        for (int w = 0; w < FP; ++w) fr[w] = rowf[r][w];
+        if (gaps_differ<FP, FU>(fr, ws.cf[c], gapf) &&
+            fields_rest_ok<FP, FU>(fr, ws.cf[c], a.d, a.sw, hashed, keepf)) {
+          ii = rowi[r];
+          jj = ws.ci[c];
+          ok = true;
+          if (rep0) {
+            int h = 0;
+#pragma unroll
+            for (int w = 0; w < FU; ++w) h += __popc(sym_diff32(rowf0[r][w] ^ ws.cf0[c][w], a.sw));
+            ok = h > a.d && replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj,
+                                                     ii < jj ? jj : ii, 1);
           }
         }
       }
+      if constexpr (FUSE) {
+        fuse_one(a, ok, ii, jj, lane, sm_q[warp], acc);
+      } else {
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        __syncwarp();
+        if (ok) sm_qs[warp][npass + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)e;
+        npass += __popc(bal);
+      }
+    }
+    if (!FUSE && npass) {
       __syncwarp();
+      if (nout + npass > (uint32_t)kOut) flush_out<FP>(a, ws, nout, lane);
+      if (npass > (uint32_t)kOut) {  // a tile with many pairs: its own append
+        unsigned long long b1 = 0;
+        if (lane == 0) b1 = atomicAdd(a.count, (unsigned long long)npass);
+        b1 = __shfl_sync(0xffffffffu, b1, 0);
+        for (uint32_t t2 = lane; t2 < npass; t2 += 32) {
+          const uint32_t e = sm_qs[warp][t2];
+          if (b1 + t2 < (unsigned long long)a.cap)
+            a.cand[b1 + t2] = ordered_pair(rowi[e >> 5], ws.ci[e & 31u]);
+        }
+      } else {
+        for (uint32_t t2 = lane; t2 < npass; t2 += 32) {
+          const uint32_t e = sm_qs[warp][t2];
+          ws.out[nout + t2] = ordered_pair(rowi[e >> 5], ws.ci[e & 31u]);
+        }
+        nout += npass;
+      }
+    }
     }
   }
   }
+  if (!FUSE) flush_out<FP>(a, ws, nout, lane);
   if constexpr (FUSE) fuse_finish(a, acc, lane);
+  if (lane == 0 && evaluated && a.evaluated) atomicAdd(a.evaluated, evaluated);
 }
 
 // Pairs of a finished list per point set: counts[set of i] += 1 for every
@@ -1200,6 +1266,7 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   a.set_off = b.set_off;
   a.nsets = b.nsets;
   a.sw = b.sw > 0 ? b.sw : 1;
+  a.evaluated = b.evaluated;
   const bool fuse = b.X != nullptr;
   if (fuse && !b.kept) return set_error("fused recheck needs counters"), MSM_E_INVAL;
   const int mb = b.min_blocks ? b.min_blocks : 4;
@@ -1207,15 +1274,17 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   MSM_CUDA(cudaMemsetAsync(g.grab, 0, sizeof(unsigned), s));
   kt_begin(KC_CHECK, s);
   if (b.fields) {
-#define MSM_LAUNCH_CF(P, U, F, M) \
-  check_fields_kernel<P, U, F, M><<<grid, kThreads, 0, s>>>(a, b.fields)
-#define MSM_CHECK_FIELDS(P, U)                                  \
-  if (!fuse && b.min_blocks == 6) MSM_LAUNCH_CF(P, U, false, 6); \
-  else if (!fuse && b.min_blocks == 8) MSM_LAUNCH_CF(P, U, false, 8); \
-  else if (!fuse) MSM_LAUNCH_CF(P, U, false, 0);                \
-  else if (mb == 2) MSM_LAUNCH_CF(P, U, true, 2);               \
-  else if (mb == 5) MSM_LAUNCH_CF(P, U, true, 5);               \
-  else MSM_LAUNCH_CF(P, U, true, 4)
+    // the kernel loops over chunks of work until none is left: one wave of
+    // as many CTAs as can be resident (or as tuned)
+    void (*kern)(CheckArgs, const uint32_t*) = nullptr;
+#define MSM_CF(P, U, F, M) kern = check_fields_kernel<P, U, F, M>
+#define MSM_CHECK_FIELDS(P, U)                          \
+  if (!fuse && b.min_blocks == 6) MSM_CF(P, U, false, 6); \
+  else if (!fuse && b.min_blocks == 8) MSM_CF(P, U, false, 8); \
+  else if (!fuse) MSM_CF(P, U, false, 0);                \
+  else if (mb == 2) MSM_CF(P, U, true, 2);               \
+  else if (mb == 5) MSM_CF(P, U, true, 5);               \
+  else MSM_CF(P, U, true, 4)
     switch (b.FU) {  // words holding fields: ceil(k / 2)
       case 1: MSM_CHECK_FIELDS(2, 1); break;
       case 2: MSM_CHECK_FIELDS(2, 2); break;
@@ -1228,7 +1297,13 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
       default: kt_end(s); return set_error("bad field word count"), MSM_E_INVAL;
     }
 #undef MSM_CHECK_FIELDS
-#undef MSM_LAUNCH_CF
+#undef MSM_CF
+    int per_sm = b.ctas_per_sm;
+    if (per_sm <= 0) {
+      MSM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
+      if (per_sm < 1) per_sm = 1;
+    }
+    kern<<<num_sms() * per_sm, kThreads, 0, s>>>(a, b.fields);
     kt_end(s);
     MSM_LAUNCH("check_fields_kernel");
     return MSM_OK;

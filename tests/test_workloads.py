@@ -25,3 +25,11 @@ def test_clustered_sets_layout():
     # sizes gives the same rows
     Y, _ = W.clustered_sets([5, 0, 40], 16, 3, 0.05, 9)
     assert np.array_equal(X[:45], Y)
+
+
+def test_clustered_words_flip_rate():
+    S = W.clustered_words(200_000, 2, 3, n_centres=1, and_depth=3)
+    bits = np.unpackbits(S.view(np.uint8), axis=-1).reshape(200_000, 128)
+    # one centre: the bits that differ from the column majority flip w.p. 1/8
+    maj = (bits.mean(0) > 0.5).astype(np.uint8)
+    assert abs((bits != maj).mean() - 0.125) < 0.002

@@ -173,6 +173,22 @@ def random_strings(n: int, ell: int, Q: int, seed: int,
     return np.bitwise_or.reduce(words, axis=3)
 
 
+def clustered_words(n: int, W: int, seed: int, n_centres: int, and_depth: int) -> np.ndarray:
+    """Packed strings uint64 [1][n][W] of 64 W bits: every string copies one
+    of ``n_centres`` random centre strings and flips each bit with
+    probability 2^-and_depth (the AND of ``and_depth`` random words), drawn
+    word-wise so that millions of strings stay cheap."""
+    rng = np.random.default_rng(seed)
+    centres = rng.integers(0, 2 ** 63, size=(n_centres, W), dtype=np.uint64) << np.uint64(1)
+    centres ^= rng.integers(0, 2, size=(n_centres, W), dtype=np.uint64)
+    out = centres[rng.integers(0, n_centres, size=n)]
+    flips = np.full((n, W), np.uint64(0xFFFFFFFFFFFFFFFF), dtype=np.uint64)
+    for _ in range(and_depth):
+        flips &= (rng.integers(0, 2 ** 63, size=(n, W), dtype=np.uint64) << np.uint64(1)) | \
+            rng.integers(0, 2, size=(n, W), dtype=np.uint64)
+    return (out ^ flips)[None]
+
+
 def to_bf16_values(x: np.ndarray) -> np.ndarray:
     """Round float32 values to the nearest bfloat16 (ties to even), returned
     as float32 holding exactly those bfloat16 values."""
