@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override n (0 = workload's)")
     ap.add_argument("--clusters", type=int, default=0,
                     help="override the number of clusters (0 = workload's)")
-    ap.add_argument("--cpu-sample", type=int, default=20000)
+    ap.add_argument("--cpu-sample", type=int, default=2000,
+                    help="CPU oracle sample, in points drawn as whole clusters of the workload's size")
     ap.add_argument("--clocks-dir", default="",
                     help="folder for the raw nvidia-smi clock samples (default: temp dir)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -638,6 +639,22 @@ def traffic_for(kind, workload):
 
 
 # ------------------------------------------------------------ CPU oracle
+def cpu_sample_points(wl, n, n_s, seed):
+    """A bounded sample of the workload for the CPU oracle: whole clusters of
+    the full workload's size (n / n_clusters points each, drawn as the
+    workload draws them), so that the pair work per point -- quadratic in the
+    cluster size -- matches the timed GPU run.  Returns (X, clusters)."""
+    per = max(1, n // wl.n_clusters)
+    nc = max(1, n_s // per)
+    return W.clustered(nc * per, wl.dim, nc, wl.sigma, seed), nc
+
+
+def cpu_sample_desc(X, nc, n, Q, extra):
+    return (f"{nc} whole clusters of the workload's size ({X.shape[0]:,} points, the "
+            f"{n:,}-point workload's cluster size, sigma and dim), the same R and Q={Q}; "
+            f"{extra}")
+
+
 def cpu_oracle_run(X, R, wl, n_s):
     import oracle
     t0 = time.perf_counter()
@@ -727,20 +744,18 @@ def run_reference(a, wl, Q):
     if rank != 0:
         return 0
     n = a.n or wl.n
-    n_s = min(n, a.cpu_sample)
-    X = W.clustered(n, wl.dim, wl.n_clusters, wl.sigma, wl.data_seed)[:n_s]
-    import oracle
-    R = oracle.gaussian(wl.r_seed, Q * wl.dim * wl.ell).reshape(Q, wl.dim, wl.ell)
+    X, nc = cpu_sample_points(wl, n, min(n, a.cpu_sample), wl.data_seed)
+    n_s = X.shape[0]
+    R = W.gaussian_R(Q, wl.dim, wl.ell, wl.r_seed)
     # warm-up loads the oracle and touches its memory: a small slice will do
     for _ in range(a.warmup):
-        cpu_oracle_run(X, R, wl, min(n_s, 2000))
+        cpu_oracle_run(X, R, wl, min(n_s, 200))
     t = 0.0
     for _ in range(a.steps):
         t += cpu_oracle_run(X, R, wl, n_s)
     ms = 1000.0 * t / a.steps
     value = n_s / (ms / 1000.0)
-    sample = (f"first {n_s:,} points of the {n:,}-point workload (same distribution, "
-              f"same R, Q={Q}); single-threaded C oracle, double precision")
+    sample = cpu_sample_desc(X, nc, n, Q, "single-threaded C oracle, double precision")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -789,9 +804,12 @@ def main():
     X = torch.from_numpy(Xh).cuda()
     seed = wl.r_seed
     stream = torch.cuda.current_stream()
+    # the projection matrix from the seeded generator the parity tests use
+    # (resident on the device like X), so the timed path is the tested one
+    Rg = torch.from_numpy(W.gaussian_R(Q, wl.dim, wl.ell, seed)).cuda()
 
     def step(xin):
-        return msm.eps_graph(xin, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=Q, seed=seed,
+        return msm.eps_graph(xin, msm.COSINE, wl.eps, wl.ell, wl.k, wl.d, Q=Q, R=Rg,
                              cand_capacity=600 * n)
 
     for _ in range(max(3, a.warmup)):
@@ -809,6 +827,7 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kms = {}
     klaunch = {}
+    phase_ms = {}
     counts = []
     e0.record(stream)
     for _ in range(a.steps):
@@ -817,6 +836,8 @@ def main():
         for kname, v in st["kernel_ms"].items():
             kms[kname] = kms.get(kname, 0.0) + v
             klaunch[kname] = klaunch.get(kname, 0) + st["kernel_launches"][kname]
+        for ph, v in st["ms"].items():
+            phase_ms[ph] = phase_ms.get(ph, 0.0) + v
         del p, dv
     e1.record(stream)
     torch.cuda.synchronize()
@@ -976,19 +997,18 @@ def main():
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        import oracle
-        n_s = min(n, a.cpu_sample)
-        R = oracle.gaussian(seed, Q * wl.dim * wl.ell).reshape(Q, wl.dim, wl.ell)
-        t = cpu_oracle_run(Xh, R, wl, n_s)
+        Xc, nc = cpu_sample_points(wl, n, min(n, a.cpu_sample), wl.data_seed + 7)
+        n_s = Xc.shape[0]
+        R = W.gaussian_R(Q, wl.dim, wl.ell, seed)
+        t = cpu_oracle_run(Xc, R, wl, n_s)
         cpu = {"value": n_s / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {n_s:,} of the {n:,} points, same R and Q={Q}; "
-                         f"single-threaded C oracle, {t:.1f} s"}
+               "sample": cpu_sample_desc(Xc, nc, n, Q, f"single-threaded C oracle, {t:.1f} s")}
         # the same run on every core of the host: independent copies
         cores = usable_cores()
         allc = None
         if cores > 1 and not a.no_cpu_all_cores:
             try:
-                res = cpu_oracle_copies(Xh, R, wl, n_s, cores)
+                res = cpu_oracle_copies(Xc, R, wl, n_s, cores)
             except Exception:  # noqa: BLE001 - a host-side measurement aid
                 res = None
             if res:
@@ -1013,6 +1033,7 @@ def main():
             "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
             "roofline": roof, "hbm_kernels": hbm_kernels,
             "kernel_ms_per_step": {k: v / a.steps for k, v in kms.items()},
+            "phase_ms_per_step": {k: v / a.steps for k, v in phase_ms.items()},
             "stats": {k: st[k] for k in ("Q", "masks", "checks", "evaluated", "cand", "type1",
                                          "proj_recompute", "dist_recompute", "overflow_retries")},
             "missing_edges": missing, "forms": forms, "cpu_baseline": cpu,

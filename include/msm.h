@@ -447,6 +447,15 @@ int msm_mlp_adam(float* params, const float* grads, float* m, float* v,
                  float eps, void* W1_bf16, void* W2_bf16, int hidden, int dim,
                  int dim_out, void* stream);
 
+/* Testing aid, not part of the method: the poll limit of the bounded waits
+ * inside the tensor-core projection (every wait also ends after 2 s of
+ * device time).  A wait that runs out makes its CTA stop, wait for the copies
+ * and MMAs it already issued, release its tensor memory and report it; the
+ * call then returns MSM_E_TIMEOUT (msm_project) and nothing faults.  0
+ * restores the default of 2^22 polls.  Applies to later calls of every
+ * thread; returns the previous limit. */
+int msm_set_wait_limit(uint32_t polls);
+
 /* Release the buffers of a msm_pairs returned by this library. */
 void msm_free_pairs(msm_pairs* p, const msm_allocator* alloc, void* stream);
 

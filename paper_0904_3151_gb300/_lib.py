@@ -64,6 +64,7 @@ class Params(ctypes.Structure):
 # Every symbol include/msm.h declares, with its ctypes signature.
 SIGNATURES = {
     "msm_version": (ctypes.c_int, []),
+    "msm_set_wait_limit": (ctypes.c_int, [ctypes.c_uint32]),
     "msm_launch_count": (ctypes.c_int64, []),
     "msm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "msm_last_error": (ctypes.c_char_p, []),

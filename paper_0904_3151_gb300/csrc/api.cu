@@ -674,6 +674,8 @@ extern "C" {
 
 int msm_version(void) { return 100; }
 
+int msm_set_wait_limit(uint32_t polls) { return set_wait_polls(polls); }
+
 int64_t msm_launch_count(void) { return (int64_t)g_launches.load(); }
 
 const char* msm_strerror(int status) {

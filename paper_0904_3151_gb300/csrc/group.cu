@@ -353,21 +353,31 @@ struct BucketSmem {
   uint32_t tmp[32];
 };
 
-// Stable rank of the digit (key >> shift) & 0xFF of the first m items held
-// in the warp-blocked order e = warp * 32 IPT + r * 32 + lane: pos[r] gets
-// the item's place in the digit-sorted order, sm.dstart the digit starts and
-// sm.wh[w][d] the count of digit d in warps before w.  Ends synchronised.
+// Items of a bucket are spread evenly over the CTA's warps in blocked order:
+// warp w holds items [w pw, (w + 1) pw), pw = the smallest multiple of 32
+// with kBT / 32 * pw >= m, lane l of round r item w pw + 32 r + l; the
+// rounds a warp runs grow with the bucket, not with the capacity.
+__device__ __forceinline__ int per_warp_items(int m) {
+  const int nw = kBT / 32;
+  return ((m + nw * 32 - 1) / (nw * 32)) * 32;
+}
+
+// Stable rank of the digit (key >> shift) & 0xFF of the first m items
+// (held as above, pw items per warp): pos[r] gets the item's place in the
+// digit-sorted order, sm.dstart the digit starts and sm.wh[w][d] the count
+// of digit d in warps before w.  Ends synchronised.
 template <int IPT>
 __device__ __forceinline__ void bucket_rank(const uint32_t (&key)[IPT], int shift, int m,
-                                            uint32_t (&pos)[IPT], BucketSmem& sm) {
-  constexpr int PER_WARP = 32 * IPT;
+                                            int pw, uint32_t (&pos)[IPT], BucketSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
+  const int rounds = pw / 32;
   for (int t = tid; t < (kBT / 32) * kRadix; t += kBT) (&sm.wh[0][0])[t] = 0;
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
-    const int e = warp * PER_WARP + r * 32 + lane;
+    if (r >= rounds || warp * pw + r * 32 >= m) break;  // warp-uniform
+    const int e = warp * pw + r * 32 + lane;
     const bool valid = e < m;
     const uint32_t digit = valid ? (key[r] >> shift) & 0xFFu : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xffffffffu, digit);
@@ -394,7 +404,8 @@ __device__ __forceinline__ void bucket_rank(const uint32_t (&key)[IPT], int shif
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
-    const int e = warp * PER_WARP + r * 32 + lane;
+    if (r >= rounds) break;
+    const int e = warp * pw + r * 32 + lane;
     if (e < m) {
       const uint32_t digit = (key[r] >> shift) & 0xFFu;
       pos[r] += sm.dstart[digit] + sm.wh[warp][digit];
@@ -408,7 +419,6 @@ __global__ void __launch_bounds__(kBT, 2)
 bucket_sort_kernel(BucketArgs a) {
   extern __shared__ __align__(16) unsigned char bucket_smem[];
   BucketSmem& sm = *reinterpret_cast<BucketSmem*>(bucket_smem);
-  constexpr int PER_WARP = 32 * kBIpt;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int seg = blockIdx.x / kRadix, digit = blockIdx.x % kRadix;
   const int64_t cb = (int64_t)seg * kRadix * a.tiles + (int64_t)digit * a.tiles;
@@ -419,21 +429,23 @@ bucket_sort_kernel(BucketArgs a) {
   if (m <= 1) return;
   uint32_t key[kBIpt], val[kBIpt], pos[kBIpt];
   if (m <= kBCap) {
+    const int pw = per_warp_items((int)m), rounds = pw / 32;
 #pragma unroll
     for (int r = 0; r < kBIpt; ++r) {
-      const int e = warp * PER_WARP + r * 32 + lane;
+      const int e = warp * pw + r * 32 + lane;
       key[r] = 0;
       val[r] = 0;
-      if (e < m) {
+      if (r < rounds && e < m) {
         key[r] = a.keys[start + e];
         val[r] = a.vals[start + e];
       }
     }
     for (int p = 0; p < a.passes; ++p) {
-      bucket_rank<kBIpt>(key, 8 * p, (int)m, pos, sm);
+      bucket_rank<kBIpt>(key, 8 * p, (int)m, pw, pos, sm);
 #pragma unroll
       for (int r = 0; r < kBIpt; ++r) {
-        const int e = warp * PER_WARP + r * 32 + lane;
+        if (r >= rounds) break;
+        const int e = warp * pw + r * 32 + lane;
         if (e < m) {
           sm.ks[pos[r]] = key[r];
           sm.vs[pos[r]] = val[r];
@@ -442,7 +454,8 @@ bucket_sort_kernel(BucketArgs a) {
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < kBIpt; ++r) {
-        const int e = warp * PER_WARP + r * 32 + lane;
+        if (r >= rounds) break;
+        const int e = warp * pw + r * 32 + lane;
         if (e < m) {
           key[r] = sm.ks[e];
           val[r] = sm.vs[e];
@@ -474,20 +487,22 @@ bucket_sort_kernel(BucketArgs a) {
     __syncthreads();
     for (int64_t c0 = 0; c0 < m; c0 += kBCap) {
       const int cm = (int)min((int64_t)kBCap, m - c0);
+      const int pw = per_warp_items(cm), rounds = pw / 32;
 #pragma unroll
       for (int r = 0; r < kBIpt; ++r) {
-        const int e = warp * PER_WARP + r * 32 + lane;
+        const int e = warp * pw + r * 32 + lane;
         key[r] = 0;
         val[r] = 0;
-        if (e < cm) {
+        if (r < rounds && e < cm) {
           key[r] = sk[c0 + e];
           val[r] = sv[c0 + e];
         }
       }
-      bucket_rank<kBIpt>(key, shift, cm, pos, sm);
+      bucket_rank<kBIpt>(key, shift, cm, pw, pos, sm);
 #pragma unroll
       for (int r = 0; r < kBIpt; ++r) {
-        const int e = warp * PER_WARP + r * 32 + lane;
+        if (r >= rounds) break;
+        const int e = warp * pw + r * 32 + lane;
         if (e < cm) {
           const uint32_t d = (key[r] >> shift) & 0xFFu;
           const uint32_t q = sm.run[d] + pos[r] - sm.dstart[d];

@@ -145,10 +145,14 @@ int launch_project(const void* X, int dtype, int64_t n, int dim,
                    int Q, int ell, uint64_t* strings,
                    unsigned long long* recompute, cudaStream_t s);
 
-// project_tc.cu: the same projection on tcgen05 tensor cores (TF32 for
-// float X, BF16 with a split R for bf16 X), TMA-fed, sign/pack in the TMEM
-// epilogue; undecided bits are queued and settled by a fix-up kernel.
+// project_tc.cu: the same projection on tcgen05 tensor cores (X and R split
+// into bf16 high and low parts, three MMAs; bf16 X needs two), TMA-fed,
+// sign/pack in the TMEM epilogue; undecided bits are queued and settled by
+// a fix-up kernel.
 bool tc_project_supported(int dtype, int dim, uintptr_t xaddr);
+// Poll limit of the projection's bounded waits (0: the default); returns
+// the previous limit.
+int set_wait_polls(uint32_t polls);
 size_t tc_project_scratch_bytes(int64_t n, int dim, int Q, int ell, int dtype);
 // *fell_back = true when the queue overflowed (the caller must then run the
 // SIMT projection, which overwrites every string).  fell_back == NULL: no

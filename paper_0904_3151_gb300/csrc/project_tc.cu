@@ -1,35 +1,59 @@
 // Step A1 on the 5th-generation tensor cores: t = X R_q for all replicates
-// as one GEMM (n x D) * (D x Q*W*64), operands staged in shared memory by
-// TMA (128-byte swizzle), accumulators in TMEM, and the sign / pack of
-// Eq. 3 fused into the TMEM read-out.  Each CTA owns 128 rows and walks all
-// column tiles of 128 columns; each epilogue thread owns one row, so a
-// 64-column half of the tile becomes one packed word without shuffles.
+// as one GEMM (n x D) * (D x Q*W*64).  Each CTA owns 128 rows of X, staged
+// once in shared memory by TMA (128-byte swizzle), and walks the column
+// tiles of 64 columns (one packed output word per row): a producer warp
+// keeps a ring of R tiles filled by TMA, an MMA warp issues the MMAs of
+// tile t into one of two TMEM accumulators, and eight epilogue warps read
+// the other accumulator (tcgen05.ld; a thread owns one row and 32 of the 64
+// columns) and turn tile t - 1 into signs and packed half-words (Eq. 3), so
+// copies, MMAs and the epilogue overlap.
 //
-// Exactness: operands are read as TF32 (X, R float: each operand within
-// 2^-10 relative) or as BF16 (X stored bf16 exactly; R split into a bf16
-// high part and a bf16 low part, two MMAs, so R is represented to 2^-16).
-// The accumulated float value t' then satisfies
-//   |t' - t| <= (e_op + 4 D 2^-24) |x| |r|,
-// with e_op = 2^-9 (TF32) or 2^-16 (BF16 split); 4 D 2^-24 is four times the
-// classical bound of the float accumulation.  Bits with |t'| within that
-// margin are written as 0 and queued; project_fix_kernel recomputes each in
-// float with its own bound and, if still undecided, in double precision by
-// sequential fma (the definition of the bit), then sets it.
+// Exactness.  Both operands are split into bf16 parts: x = xh + xl + ex with
+// xh = bf16(x), xl = bf16(x - xh), |ex| <= 2^-16 |x| (bf16 keeps 8
+// significant bits), and likewise r = rh + rl + er (bf16 X is exact: xl = 0).
+// The three MMAs xh rh + xh rl + xl rh (kind::f16, float accumulation)
+// leave out xl rl + (xh + xl) er + ex (rh + rl), at most 3.1 2^-16 |x_c r_c|
+// per coordinate, so with sum_c |x_c r_c| <= |x| |r| the accumulated t'
+// satisfies
+//   |t' - t| <= (3.125 2^-16 + 4 m 2^-24) |x| |r| + tiny,
+// m = the number of accumulated products (3 D, or 2 D for bf16 X); 4 m 2^-24
+// is four times the classical bound of the float accumulation.  Bits with
+// |t'| within that margin are written as 0 and queued; project_fix_kernel
+// recomputes each in float with its own bound and, if still undecided, in
+// double precision by sequential fma (the definition of the bit), then sets
+// it.
+//
+// Every wait is bounded (a poll limit and 2 s of %globaltimer); a thread that
+// gives up raises a CTA flag and the status word, the others stop at their
+// next wait, and the producer and MMA threads wait (bounded, ignoring the
+// flag) for every copy and MMA they issued before the CTA releases its
+// shared memory and TMEM.
+#include <atomic>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "msm_internal.cuh"
 
 namespace msm {
+
+// Poll limit of the projection's bounded waits (a testing knob).
+static std::atomic<uint32_t> g_wait_polls{1u << 22};
+
 namespace {
 
-constexpr int kRows = 128;      // M of the MMA, rows per CTA
-constexpr int kCols = 64;       // N of the MMA, columns per tile (one word)
-constexpr int kChunkBytes = 128;  // K bytes per swizzle atom row
-constexpr int kMaxChunks = 4;   // K chunks kept resident (D*esize <= 512 B)
-constexpr int kTileBytes = kRows * kChunkBytes;  // one 128 x 128 B box of X
-constexpr int kBTileBytes = kCols * kChunkBytes; // one 64 x 128 B box of R
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr int kRows = 128;          // M of the MMA, rows per CTA
+constexpr int kCols = 64;           // N of the MMA, columns per tile (one word)
+constexpr int kChunkBytes = 128;    // K bytes per swizzle atom row (64 bf16)
+constexpr int kMaxChunks = 4;       // bf16 rows of at most 512 B (dim <= 256)
+constexpr int kXBox = kRows * kChunkBytes;  // one 128 x 128 B box of X
+constexpr int kRBox = kCols * kChunkBytes;  // one 64 x 128 B box of R
+constexpr int kMaxStages = 4;       // R tiles in flight
+constexpr int kEpiWarps = 8;        // warp w: TMEM lanes (rows) 32 (w % 4) ..,
+                                    // columns 32 (w / 4) .. of each tile
+constexpr int kTcThreads = (kEpiWarps + 2) * 32;  // + TMA warp + MMA warp
+constexpr uint32_t kDrainPolls = 1u << 24;
+constexpr size_t kSmemBudget = 200 * 1024;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -52,13 +76,13 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 
 // Bounded wait on an mbarrier phase: gives up (returns false) after
-// kWaitLimit polls, after 2 s of wall-clock time, or as soon as another CTA
-// has reported a failure in *status.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
-                                          const unsigned* status) {
+// `polls` polls, after 2 s of wall-clock time, or as soon as another thread
+// of the CTA has raised *abortf (when given).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t polls,
+                                          const uint32_t* abortf) {
   const uint32_t a = saddr(bar);
   const uint64_t t0 = globaltimer_ns();
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+  for (uint32_t i = 0; i < polls; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -67,12 +91,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
-    if ((i & 255u) == 255u) {
+    if ((i & 63u) == 63u) {
+      if (abortf && *(volatile const uint32_t*)abortf) return false;
       if (globaltimer_ns() - t0 > 2000000000ull) return false;
-      if (status && *(volatile const unsigned*)status) return false;
     }
   }
   return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map,
@@ -140,9 +168,11 @@ struct TcArgs {
   int64_t n;
   int dim;
   int ell, W, Q;
-  int ctiles;          // column tiles of 128 over the padded Q*W*64 columns
-  int chunks;          // K chunks of 128 B
+  int ctiles;          // column tiles of 64 over the padded Q*W*64 columns
+  int chunks;          // K chunks of 128 B of the bf16 operands
+  int stages;          // R tiles in the ring
   uint32_t idesc;
+  uint32_t polls;      // poll limit of the bounded waits
   float mscale, mabs;  // margin = mscale * |x| * |r| + mabs
   const float* xnorm;  // [n]
   const float* rnorm;  // [Q * W * 64] (padded columns have norm 0)
@@ -153,36 +183,49 @@ struct TcArgs {
   unsigned* status;    // bit 0: a bounded wait gave up
 };
 
-// 128 threads: warp 0 also allocates TMEM; thread 0 issues TMA and MMA; all
-// four warps read TMEM (warp w owns lanes 32w..32w+31 = rows).
-template <bool BF16>
-__global__ void __launch_bounds__(128, 2)
+// 320 threads: warps 0-7 epilogue (warp 0 also allocates TMEM), warp 8 lane
+// 0 issues the TMA copies, warp 9 lane 0 the MMAs.
+template <bool XLO>
+__global__ void __launch_bounds__(kTcThreads, 1)
 project_tc_kernel(const __grid_constant__ CUtensorMap tmX,
-                  const __grid_constant__ CUtensorMap tmB,
-                  const __grid_constant__ CUtensorMap tmB2, TcArgs a) {
+                  const __grid_constant__ CUtensorMap tmXl,
+                  const __grid_constant__ CUtensorMap tmR,
+                  const __grid_constant__ CUtensorMap tmRl, TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  constexpr int kNB = BF16 ? 2 : 1;  // B operands (R high, R low)
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = base;
-  uint8_t* sB = base + a.chunks * kTileBytes;  // then kNB * chunks boxes of R
-  uint64_t* bars = (uint64_t*)(sB + kNB * a.chunks * kBTileBytes);
-  uint32_t* tslot = (uint32_t*)(bars + 4);
-  uint64_t* barA = bars;
-  uint64_t* barB = bars + 1;
-  uint64_t* barM = bars + 2;
+  const int xbytes = a.chunks * kXBox;
+  const int rbytes = a.chunks * kRBox;  // one part (high or low) of an R tile
+  uint8_t* sX = base;
+  uint8_t* sXl = base + xbytes;
+  uint8_t* sR = base + (XLO ? 2 : 1) * xbytes;  // stage s: high, then low
+  uint64_t* bars = (uint64_t*)(sR + a.stages * 2 * rbytes);
+  uint64_t* barX = bars;
+  uint64_t* full = bars + 1;
+  uint64_t* empty = full + a.stages;
+  uint64_t* tfull = empty + a.stages;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tslot = (uint32_t*)(tempty + 2);
+  uint32_t* abortf = tslot + 1;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row0 = (int64_t)blockIdx.x * kRows;
   if (tid == 0) {
-    mbar_init(barA, 1);
-    mbar_init(barB, 1);
-    mbar_init(barM, 1);
+    mbar_init(barX, 1);
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, kEpiWarps);
+    }
+    *abortf = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      saddr(tslot)),
-                 "r"(kCols)
+                 "r"(2 * kCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -190,125 +233,189 @@ project_tc_kernel(const __grid_constant__ CUtensorMap tmX,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  bool failed = false;
+  const int ksteps = kChunkBytes / 32;  // MMA K is 32 bytes (16 bf16)
 
-  if (tid == 0) {
-    mbar_expect_tx(barA, (uint32_t)(a.chunks * kTileBytes));
-    for (int c = 0; c < a.chunks; ++c)
-      tma_load_2d(sA + c * kTileBytes, &tmX, barA, c * (kChunkBytes / (BF16 ? 2 : 4)),
-                  (int)row0);
-  }
-  const int64_t row = row0 + warp * 32 + lane;
-  const float xn = row < a.n ? a.xnorm[row] : 0.f;
-  const int colsPerRep = a.W * 64;
-  const int ksteps = kChunkBytes / 32;  // MMA K is 32 bytes for both kinds
-
-  for (int ct = 0; ct < a.ctiles && !failed; ++ct) {
-    const uint32_t par = ct & 1;
-    if (tid == 0) {
-      mbar_expect_tx(barB, (uint32_t)(kNB * a.chunks * kBTileBytes));
+  if (warp == kEpiWarps) {
+    // TMA producer: X once, then R tiles into the ring as stages free up
+    if (lane == 0) {
+      int last_t[kMaxStages];  // last tile loaded into each stage (-1: none)
+      for (int s = 0; s < kMaxStages; ++s) last_t[s] = -1;
+      mbar_expect_tx(barX, (uint32_t)((XLO ? 2 : 1) * xbytes));
       for (int c = 0; c < a.chunks; ++c) {
-        const int kx = c * (kChunkBytes / (BF16 ? 2 : 4));
-        tma_load_2d(sB + c * kBTileBytes, &tmB, barB, kx, ct * kCols);
-        if (BF16)
-          tma_load_2d(sB + (a.chunks + c) * kBTileBytes, &tmB2, barB, kx, ct * kCols);
+        tma_load_2d(sX + c * kXBox, &tmX, barX, c * (kChunkBytes / 2), (int)row0);
+        if (XLO) tma_load_2d(sXl + c * kXBox, &tmXl, barX, c * (kChunkBytes / 2), (int)row0);
       }
-      bool ok = (ct > 0 || mbar_wait(barA, 0, a.status)) && mbar_wait(barB, par, a.status);
-      if (ok) {
+      bool ok = true;
+      for (int t = 0; t < a.ctiles; ++t) {
+        const int s = t % a.stages, k = t / a.stages;
+        if (k > 0) {  // the MMAs of tile t - stages are done with this stage
+          ok = mbar_wait(empty + s, (uint32_t)((k - 1) & 1), a.polls, abortf);
+          if (!ok) break;
+        }
+        mbar_expect_tx(full + s, (uint32_t)(2 * rbytes));
+        uint8_t* dst = sR + s * 2 * rbytes;
+        for (int c = 0; c < a.chunks; ++c) {
+          tma_load_2d(dst + c * kRBox, &tmR, full + s, c * (kChunkBytes / 2), t * kCols);
+          tma_load_2d(dst + rbytes + c * kRBox, &tmRl, full + s, c * (kChunkBytes / 2),
+                      t * kCols);
+        }
+        last_t[s] = t;
+      }
+      if (!ok) {
+        atomicOr(a.status, 1u);
+        *(volatile uint32_t*)abortf = 1u;
+      }
+      // drain: every copy issued lands before the CTA releases its memory
+      // (the loads of one stage complete in order, so the last one suffices)
+      mbar_wait(barX, 0, kDrainPolls, nullptr);
+      for (int s = 0; s < a.stages; ++s)
+        if (last_t[s] >= 0)
+          mbar_wait(full + s, (uint32_t)((last_t[s] / a.stages) & 1), kDrainPolls, nullptr);
+    }
+  } else if (warp == kEpiWarps + 1) {
+    // MMA issuer: tile t into accumulator t & 1 once its R tile has landed
+    // and the epilogue has read that accumulator's previous tile
+    if (lane == 0) {
+      int last_tb = -1, last_es = -1;
+      uint32_t last_tpar = 0, last_epar = 0;
+      bool ok = mbar_wait(barX, 0, a.polls, abortf);
+      for (int t = 0; ok && t < a.ctiles; ++t) {
+        const int s = t % a.stages, b = t & 1;
+        const uint32_t sp = (uint32_t)((t / a.stages) & 1), bp = (uint32_t)((t >> 1) & 1);
+        ok = mbar_wait(full + s, sp, a.polls, abortf);
+        if (!ok) break;
+        if (t >= 2) {
+          ok = mbar_wait(tempty + b, bp ^ 1u, a.polls, abortf);
+          if (!ok) break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(b * kCols);
+        const uint8_t* rs = sR + s * 2 * rbytes;
         uint32_t acc = 0;
         for (int c = 0; c < a.chunks; ++c)
           for (int ks = 0; ks < ksteps; ++ks) {
-            const uint64_t ad = sw128_desc(saddr(sA + c * kTileBytes) + ks * 32);
-            const uint64_t bd = sw128_desc(saddr(sB + c * kBTileBytes) + ks * 32);
-            mma<BF16>(tmem, ad, bd, a.idesc, acc);
+            const uint64_t ah = sw128_desc(saddr(sX + c * kXBox) + ks * 32);
+            const uint64_t bh = sw128_desc(saddr(rs + c * kRBox) + ks * 32);
+            const uint64_t bl = sw128_desc(saddr(rs + rbytes + c * kRBox) + ks * 32);
+            mma<true>(d, ah, bh, a.idesc, acc);
             acc = 1;
-            if (BF16) {
-              const uint64_t bd2 = sw128_desc(saddr(sB + (a.chunks + c) * kBTileBytes) + ks * 32);
-              mma<BF16>(tmem, ad, bd2, a.idesc, 1);
+            mma<true>(d, ah, bl, a.idesc, 1);
+            if (XLO) {
+              const uint64_t al = sw128_desc(saddr(sXl + c * kXBox) + ks * 32);
+              mma<true>(d, al, bh, a.idesc, 1);
             }
           }
-        mma_commit(barM);
-      } else {
+        mma_commit(tfull + b);
+        mma_commit(empty + s);
+        last_tb = b;
+        last_tpar = bp;
+        last_es = s;
+        last_epar = sp;
+      }
+      if (!ok) {
         atomicOr(a.status, 1u);
+        *(volatile uint32_t*)abortf = 1u;
       }
+      // drain: every MMA issued (and its commits) completes before the CTA
+      // releases its tensor memory
+      if (last_tb >= 0) mbar_wait(tfull + last_tb, last_tpar, kDrainPolls, nullptr);
+      if (last_es >= 0) mbar_wait(empty + last_es, last_epar, kDrainPolls, nullptr);
     }
-    // Every thread waits for the accumulators (a failed issue never
-    // commits, so this wait also runs out); the CTA agrees on the outcome
-    // so that all threads leave the loop together.
-    const bool ok = mbar_wait(barM, par, a.status);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(a.status, 1u);
-      failed = true;
-      // let this tile's copies land before the CTA's memory is released
-      if (tid == 0) {
-        mbar_wait(barB, par, nullptr);
-        if (ct == 0) mbar_wait(barA, 0, nullptr);
-      }
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+  } else if (warp < kEpiWarps) {
+    // epilogue: rows 32 (warp % 4) + lane, columns 32 (warp / 4) .. + 31 of
+    // every tile (a warp may read only its quarter of the TMEM lanes)
+    const int quarter = warp & 3, half = warp >> 2;
+    const int64_t row = row0 + quarter * 32 + lane;
     const bool live_row = row < a.n;
-    for (int half = 0; half < kCols / 64; ++half) {
-      const int gcol0 = ct * kCols + half * 64;  // first column of this word
+    const float xn = live_row ? a.xnorm[row] : 0.f;
+    const int colsPerRep = a.W * 64;
+    const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+    uint32_t* strings32 = reinterpret_cast<uint32_t*>(a.strings);
+    for (int t = 0; t < a.ctiles; ++t) {
+      const int b = t & 1;
+      const uint32_t bp = (uint32_t)((t >> 1) & 1);
+      const bool ok = mbar_wait(tfull + b, bp, a.polls, abortf);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) {
+          atomicOr(a.status, 1u);
+          *(volatile uint32_t*)abortf = 1u;
+        }
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t r[32];
+      tmem_ld32(tlane + (uint32_t)(b * kCols), r);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + b);
+      const int gcol0 = t * kCols;             // first column of this word
       const int q = gcol0 / colsPerRep;
-      const int cw = gcol0 % colsPerRep;         // column of the word in R_q
+      const int cw = gcol0 % colsPerRep + half * 32;  // first column of this half in R_q
       const bool live = live_row && q < a.Q;
-      uint64_t word = 0;
-      for (int part = 0; part < 2; ++part) {
-        uint32_t r[32];
-        tmem_ld32(tbase + half * 64 + part * 32, r);
-        uint32_t flagged = 0;
-        if (live) {
+      uint32_t bits = 0, flagged = 0;
+      if (live) {
+        const float* rn = a.rnorm + q * colsPerRep + cw;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = cw + part * 32 + j;
-            if (c >= a.ell) continue;
-            const float t = __uint_as_float(r[j]);
-            const float m = a.mscale * xn * a.rnorm[q * colsPerRep + c] + a.mabs;
-            if (fabsf(t) <= m) flagged |= 1u << j;
-            else if (t > 0.f) word |= 1ull << (part * 32 + j);
-          }
-        }
-        // queue the undecided bits: one atomic per warp
-        uint32_t cnt = __popc(flagged), incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total) {
-          unsigned long long b0 = 0;
-          if (lane == 31) b0 = atomicAdd(a.fix_count, (unsigned long long)total);
-          b0 = __shfl_sync(0xffffffffu, b0, 31) + (incl - cnt);
-          while (flagged) {
-            const int j = __ffs(flagged) - 1;
-            flagged &= flagged - 1;
-            if ((int64_t)b0 < a.fix_cap)
-              a.fix[b0] = ((uint64_t)row << 32) | (uint32_t)(q * a.ell + cw + part * 32 + j);
-            ++b0;
-          }
+        for (int j = 0; j < 32; ++j) {
+          if (cw + j >= a.ell) continue;
+          const float tv = __uint_as_float(r[j]);
+          const float m = a.mscale * xn * rn[j] + a.mabs;
+          if (fabsf(tv) <= m) flagged |= 1u << j;
+          else if (tv > 0.f) bits |= 1u << j;
         }
       }
-      if (live) a.strings[((size_t)q * a.n + row) * a.W + cw / 64] = word;
+      // queue the undecided bits: one atomic per warp
+      uint32_t cnt = __popc(flagged), incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      if (total) {
+        unsigned long long b0 = 0;
+        if (lane == 31) b0 = atomicAdd(a.fix_count, (unsigned long long)total);
+        b0 = __shfl_sync(0xffffffffu, b0, 31) + (incl - cnt);
+        while (flagged) {
+          const int j = __ffs(flagged) - 1;
+          flagged &= flagged - 1;
+          if ((int64_t)b0 < a.fix_cap)
+            a.fix[b0] = ((uint64_t)row << 32) | (uint32_t)(q * a.ell + cw + j);
+          ++b0;
+        }
+      }
+      // the low (half 0) or high (half 1) 32 bits of the word, little-endian
+      if (live) strings32[(((size_t)q * a.n + row) * a.W + cw / 64) * 2 + half] = bits;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * kCols)
                  : "memory");
 }
 
-// Rt[q * W * 64 + c][k] = R[q][k][c] for c < ell, 0 otherwise; rows padded
-// to a multiple of 128.  BF16: hi = bf16(R), lo = bf16(R - hi).
-template <bool BF16>
-__global__ void transpose_R_kernel(const float* R, int Q, int dim, int ell,
-                                   int W, int64_t rows, void* hi, void* lo,
-                                   float* rnorm) {
+// Xh = bf16(x), Xl = bf16(x - Xh) for float X (8 elements per step).
+__global__ void split_x_kernel(const float* X, int64_t count, __nv_bfloat16* Xh,
+                               __nv_bfloat16* Xl) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float v = X[e];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    Xh[e] = h;
+    Xl[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// Rows of the transposed R: row q * W * 64 + c holds column c of R_q (zero
+// for c >= ell; rows padded to a multiple of 64), as bf16 high and low parts
+// (hi = bf16(R), lo = bf16(R - hi)) for the MMAs and as float for the
+// fix-up's coalesced reads; rnorm = the column norms.
+__global__ void transpose_R_kernel(const float* R, int Q, int dim, int ell, int W,
+                                   int64_t rows, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                   float* Rt, float* rnorm) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < rows;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int colsPerRep = W * 64;
@@ -318,14 +425,10 @@ __global__ void transpose_R_kernel(const float* R, int Q, int dim, int ell,
     for (int k = 0; k < dim; ++k) {
       const float v = live ? R[((size_t)q * dim + k) * ell + c] : 0.f;
       nrm = fma((double)v, (double)v, nrm);
-      if constexpr (BF16) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-        reinterpret_cast<__nv_bfloat16*>(hi)[t * dim + k] = h;
-        reinterpret_cast<__nv_bfloat16*>(lo)[t * dim + k] = l;
-      } else {
-        reinterpret_cast<float*>(hi)[t * dim + k] = v;
-      }
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      hi[t * dim + k] = h;
+      lo[t * dim + k] = __float2bfloat16_rn(v - __bfloat162float(h));
+      Rt[t * dim + k] = v;
     }
     if (t < (int64_t)Q * colsPerRep) rnorm[t] = (float)sqrt(nrm);
   }
@@ -337,18 +440,18 @@ __device__ __forceinline__ float ldx(const void* X, int dtype, int64_t i) {
   return reinterpret_cast<const float*>(X)[i];
 }
 
-// One warp per queued bit: float dot with its own bound, then the
-// double-precision sequential-fma value when still undecided.
-// Rt: optional transposed float copy of R (row q * W * 64 + c holds column c
-// of R_q, contiguous over the coordinates); the values are R's, only the
-// loads of a column become coalesced.
+// Four queued bits per warp, eight lanes each: the float dot product with
+// its own bound decides the bit where it can; the rest go to a second queue
+// for project_fix64_kernel.  Rt: the transposed float copy of R (row
+// q * W * 64 + c holds column c of R_q, contiguous over the coordinates).
 __global__ void project_fix_kernel(const void* X, int dtype, int64_t n, int dim,
-                                   const float* R, const float* Rt, int ell, int W,
+                                   const float* Rt, int ell, int W,
                                    const float* xnorm, const float* rnorm_pad,
                                    const uint64_t* fix,
                                    const unsigned long long* fix_count,
-                                   int64_t fix_cap, uint64_t* strings,
-                                   unsigned long long* recompute, unsigned* status) {
+                                   int64_t fix_cap, uint64_t* dq,
+                                   unsigned long long* dq_count, int64_t dq_cap,
+                                   uint64_t* strings, unsigned* status) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -360,7 +463,6 @@ __global__ void project_fix_kernel(const void* X, int dtype, int64_t n, int dim,
     return;
   }
   const float m2 = (float)(2 * dim + 8) * 0x1.0p-24f;
-  // four queued signs per warp, eight lanes each (more loads in flight)
   const int sub = lane & 7, grp = lane >> 3;
   for (int64_t base = warp * 4; base < m; base += nwarps * 4) {
     const int64_t it = base + grp;
@@ -369,32 +471,53 @@ __global__ void project_fix_kernel(const void* X, int dtype, int64_t n, int dim,
     const int64_t row = (int64_t)(e >> 32);
     const int qc = (int)(e & 0xffffffffu);
     const int q = qc / ell, c = qc % ell;
-    const float* Rq = R + (size_t)q * dim * ell;
-    const float* rc = Rt ? Rt + (size_t)(q * W * 64 + c) * dim : nullptr;
+    const float* rc = Rt + (size_t)(q * W * 64 + c) * dim;
     float acc = 0.f;
-    if (valid)
-      for (int k = sub; k < dim; k += 8)
-        acc = fmaf(ldx(X, dtype, row * dim + k), rc ? rc[k] : Rq[(size_t)k * ell + c], acc);
+    if (valid) {
+#pragma unroll 4
+      for (int k = sub; k < dim; k += 8) acc = fmaf(ldx(X, dtype, row * dim + k), rc[k], acc);
+    }
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (valid && sub == 0) {
-      bool bit;
       const float marg = m2 * xnorm[row] * rnorm_pad[q * W * 64 + c] + (float)dim * 0x1.0p-120f;
       if (fabsf(acc) <= marg) {
-        double t = 0.0;
-        for (int k = 0; k < dim; ++k)
-          t = fma((double)ldx(X, dtype, row * dim + k),
-                  (double)(rc ? rc[k] : Rq[(size_t)k * ell + c]), t);
-        bit = t > 0.0;
-        atomicAdd(recompute, 1ull);
-      } else {
-        bit = acc > 0.f;
-      }
-      if (bit)
+        const unsigned long long slot = atomicAdd(dq_count, 1ull);
+        if ((int64_t)slot < dq_cap) dq[slot] = e;
+        else atomicOr(status, 2u);
+      } else if (acc > 0.f) {
         atomicOr(reinterpret_cast<unsigned long long*>(strings) + ((size_t)q * n + row) * W + c / 64,
                  1ull << (c & 63));
+      }
     }
   }
+}
+
+// One queued bit per thread: the double-precision dot product accumulated
+// by sequential fma over the coordinates -- the definition of the bit.
+__global__ void project_fix64_kernel(const void* X, int dtype, int64_t n, int dim,
+                                     const float* Rt, int ell, int W, const uint64_t* dq,
+                                     const unsigned long long* dq_count, int64_t dq_cap,
+                                     uint64_t* strings, unsigned long long* recompute) {
+  int64_t m = (int64_t)*dq_count;
+  if (m > dq_cap) m = dq_cap;  // an overflow is reported in the status word
+  unsigned long long cnt = 0;
+  for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < m;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t e = dq[it];
+    const int64_t row = (int64_t)(e >> 32);
+    const int qc = (int)(e & 0xffffffffu);
+    const int q = qc / ell, c = qc % ell;
+    const float* rc = Rt + (size_t)(q * W * 64 + c) * dim;
+    double t = 0.0;
+    for (int k = 0; k < dim; ++k) t = fma((double)ldx(X, dtype, row * dim + k), (double)rc[k], t);
+    if (t > 0.0)
+      atomicOr(reinterpret_cast<unsigned long long*>(strings) + ((size_t)q * n + row) * W + c / 64,
+               1ull << (c & 63));
+    ++cnt;
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(recompute, cnt);
 }
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -417,39 +540,58 @@ EncodeFn get_encode() {
   return fn;
 }
 
-// 2-D map over a row-major [rows][inner] matrix, box = 128 B x 128 rows.
-int make_map(CUtensorMap* m, const void* ptr, bool bf16, int64_t inner,
-             int64_t rows, int box_rows) {
+// 2-D map over a row-major bf16 [rows][inner] matrix, box = 128 B x
+// box_rows; elements past `inner` read as zero.
+int make_map(CUtensorMap* m, const void* ptr, int64_t inner, int64_t rows, int box_rows) {
   EncodeFn enc = get_encode();
   if (!enc) return set_error("cuTensorMapEncodeTiled unavailable"), MSM_E_CUDA;
-  const int es = bf16 ? 2 : 4;
   cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-  cuuint64_t gstride[1] = {(cuuint64_t)(inner * es)};
-  cuuint32_t box[2] = {(cuuint32_t)(kChunkBytes / es), (cuuint32_t)box_rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)(inner * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)(kChunkBytes / 2), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                   2, const_cast<void*>(ptr), gdim, gstride, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), gdim,
+                   gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error("cuTensorMapEncodeTiled failed (%d)", (int)r), MSM_E_CUDA;
   return MSM_OK;
 }
 
+inline size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int chunks_of(int dim) { return (2 * dim + kChunkBytes - 1) / kChunkBytes; }
+
+int stages_for(int dim, bool xlo) {
+  const size_t x = (size_t)(xlo ? 2 : 1) * chunks_of(dim) * kXBox;
+  const size_t st = (size_t)2 * chunks_of(dim) * kRBox;
+  if (x + st > kSmemBudget) return 0;
+  size_t n = (kSmemBudget - x) / st;
+  return (int)(n > (size_t)kMaxStages ? kMaxStages : n);
+}
+
 }  // namespace
 
+int set_wait_polls(uint32_t polls) {
+  const uint32_t old = g_wait_polls.exchange(polls ? polls : (1u << 22));
+  return (int)old;
+}
+
+// Rows of X as bf16 whose row stride is a multiple of 16 bytes, at most 512
+// bytes (dim <= 256), from a 16-byte-aligned address.
 bool tc_project_supported(int dtype, int dim, uintptr_t xaddr) {
-  const int es = dtype == MSM_DT_BF16 ? 2 : 4;
-  const int64_t rowbytes = (int64_t)dim * es;
-  return rowbytes % kChunkBytes == 0 && rowbytes <= kMaxChunks * kChunkBytes &&
-         (xaddr % 16) == 0;
+  if (dim < 8 || dim % 8 != 0 || chunks_of(dim) > kMaxChunks) return false;
+  if (dtype == MSM_DT_BF16 && (xaddr % 16) != 0) return false;
+  return stages_for(dim, dtype != MSM_DT_BF16) >= 1;
 }
 
 size_t tc_project_scratch_bytes(int64_t n, int dim, int Q, int ell, int dtype) {
   const int W = (ell + 63) / 64;
   const int64_t rows = (((int64_t)Q * W * 64 + kCols - 1) / kCols) * kCols;
-  const int es = dtype == MSM_DT_BF16 ? 2 : 4;
-  const int64_t fix_cap = ((int64_t)n * Q * ell) / 16 + (1 << 20);
-  return 2 * (size_t)rows * dim * es + 4 * (size_t)rows + 8 * (size_t)fix_cap + 4096;
+  const int64_t fix_cap = ((int64_t)n * Q * ell) / 64 + (1 << 20);
+  const size_t xs = dtype == MSM_DT_BF16 ? 0 : 2 * up256(2 * (size_t)n * dim);
+  return xs + 2 * up256(2 * (size_t)rows * dim) + up256(4 * (size_t)rows * dim) +
+         up256(4 * (size_t)rows) + up256(8 * (size_t)fix_cap) + up256(2 * (size_t)fix_cap) +
+         4096;
 }
 
 int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
@@ -457,34 +599,51 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
                       uint64_t* strings, unsigned long long* recompute,
                       void* ws, unsigned* status, bool* fell_back,
                       cudaStream_t s) {
-  const bool bf16 = dtype == MSM_DT_BF16;
-  const int es = bf16 ? 2 : 4;
+  const bool xlo = dtype != MSM_DT_BF16;
   const int W = (ell + 63) / 64;
   const int64_t rows = (((int64_t)Q * W * 64 + kCols - 1) / kCols) * kCols;
-  const int64_t fix_cap = ((int64_t)n * Q * ell) / 16 + (1 << 20);
+  const int64_t fix_cap = ((int64_t)n * Q * ell) / 64 + (1 << 20);
   char* p = (char*)ws;
-  void* Bhi = p; p += (size_t)rows * dim * es;
-  void* Blo = p; p += (size_t)rows * dim * es;
-  float* rnorm = (float*)p; p += 4 * (size_t)rows;
-  p = (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
-  uint64_t* fix = (uint64_t*)p; p += 8 * (size_t)fix_cap;
-  unsigned long long* fix_count = (unsigned long long*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+  __nv_bfloat16* Xh = nullptr;
+  __nv_bfloat16* Xl = nullptr;
+  if (xlo) {
+    Xh = (__nv_bfloat16*)p; p += up256(2 * (size_t)n * dim);
+    Xl = (__nv_bfloat16*)p; p += up256(2 * (size_t)n * dim);
+  }
+  __nv_bfloat16* Rh = (__nv_bfloat16*)p; p += up256(2 * (size_t)rows * dim);
+  __nv_bfloat16* Rl = (__nv_bfloat16*)p; p += up256(2 * (size_t)rows * dim);
+  float* Rt = (float*)p; p += up256(4 * (size_t)rows * dim);
+  float* rnorm = (float*)p; p += up256(4 * (size_t)rows);
+  uint64_t* fix = (uint64_t*)p; p += up256(8 * (size_t)fix_cap);
+  const int64_t dq_cap = fix_cap / 4;  // bits left undecided by the float pass
+  uint64_t* dq = (uint64_t*)p; p += up256(2 * (size_t)fix_cap);
+  unsigned long long* fix_count = (unsigned long long*)p;
+  unsigned long long* dq_count = fix_count + 1;
   if (fell_back) *fell_back = false;
 
-  MSM_CUDA(cudaMemsetAsync(fix_count, 0, 8, s));
+  MSM_CUDA(cudaMemsetAsync(fix_count, 0, 16, s));
   MSM_CUDA(cudaMemsetAsync(rnorm, 0, 4 * (size_t)rows, s));
   {
     int grid = (int)((rows + 255) / 256);
     kt_begin(KC_OTHER, s);
-    if (bf16) transpose_R_kernel<true><<<grid, 256, 0, s>>>(R, Q, dim, ell, W, rows, Bhi, Blo, rnorm);
-    else transpose_R_kernel<false><<<grid, 256, 0, s>>>(R, Q, dim, ell, W, rows, Bhi, Blo, rnorm);
+    transpose_R_kernel<<<grid, 256, 0, s>>>(R, Q, dim, ell, W, rows, Rh, Rl, Rt, rnorm);
     kt_end(s);
     MSM_LAUNCH("transpose_R_kernel");
   }
-  CUtensorMap mX, mB, mB2;
-  int rc = make_map(&mX, X, bf16, dim, n, kRows);
-  if (!rc) rc = make_map(&mB, Bhi, bf16, dim, rows, kCols);
-  if (!rc) rc = make_map(&mB2, bf16 ? Blo : Bhi, bf16, dim, rows, kCols);
+  if (xlo) {
+    int64_t grid = ((int64_t)n * dim + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (grid > cap) grid = cap;
+    kt_begin(KC_PROJECT, s);
+    split_x_kernel<<<(int)grid, 256, 0, s>>>((const float*)X, (int64_t)n * dim, Xh, Xl);
+    kt_end(s);
+    MSM_LAUNCH("split_x_kernel");
+  }
+  CUtensorMap mX, mXl, mR, mRl;
+  int rc = make_map(&mX, xlo ? (const void*)Xh : X, dim, n, kRows);
+  if (!rc) rc = make_map(&mXl, xlo ? (const void*)Xl : X, dim, n, kRows);
+  if (!rc) rc = make_map(&mR, Rh, dim, rows, kCols);
+  if (!rc) rc = make_map(&mRl, Rl, dim, rows, kCols);
   if (rc) return rc;
 
   TcArgs a;
@@ -494,14 +653,15 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
   a.W = W;
   a.Q = Q;
   a.ctiles = (int)(rows / kCols);
-  a.chunks = (dim * es) / kChunkBytes;
-  // instruction descriptor: D f32, A/B = TF32 (2) or BF16 (1), both
-  // K-major, N = 128, M = 128
-  const uint32_t fmt = bf16 ? 1u : 2u;
-  a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kCols >> 3) << 17) |
+  a.chunks = chunks_of(dim);
+  a.stages = stages_for(dim, xlo);
+  if (a.stages < 1) return set_error("no tensor-core projection for dim %d", dim), MSM_E_INVAL;
+  // instruction descriptor: D f32, A/B = BF16, both K-major, N = 64, M = 128
+  a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kCols >> 3) << 17) |
             ((uint32_t)(kRows >> 4) << 24);
-  const float eop = bf16 ? 0x1.0p-16f : 0x1.0p-9f;
-  a.mscale = eop + (float)(4 * dim) * 0x1.0p-24f;
+  a.polls = g_wait_polls.load();
+  const int terms = (xlo ? 3 : 2) * dim;
+  a.mscale = 0x1.9p-15f + (float)(4 * terms + 8) * 0x1.0p-24f;
   a.mabs = (float)dim * 0x1.0p-120f;
   a.xnorm = xnorm;
   a.rnorm = rnorm;
@@ -511,29 +671,31 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
   a.fix_count = fix_count;
   a.status = status;
 
-  const int kNB = bf16 ? 2 : 1;
-  // X tile (chunks boxes of 128 rows) + R tile (kNB * chunks boxes of 64
-  // rows) + barriers: 97 KB for float rows of 512 B, so two CTAs share an
-  // SM and one's epilogue overlaps the other's copies and MMAs
-  const size_t smem = 1024 + (size_t)a.chunks * (kTileBytes + kNB * kBTileBytes) + 64;
-  auto kern = bf16 ? project_tc_kernel<true> : project_tc_kernel<false>;
+  // X tile (high [+ low]) + the ring of R tiles (high + low) + barriers
+  const size_t smem = 1024 + (size_t)(xlo ? 2 : 1) * a.chunks * kXBox +
+                      (size_t)a.stages * 2 * a.chunks * kRBox + 8 * (1 + 2 * kMaxStages + 4) + 64;
+  auto kern = xlo ? project_tc_kernel<true> : project_tc_kernel<false>;
   MSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned grid = (unsigned)((n + kRows - 1) / kRows);
   kt_begin(KC_PROJECT, s);
-  kern<<<grid, 128, smem, s>>>(mX, mB, mB2, a);
+  kern<<<grid, kTcThreads, smem, s>>>(mX, mXl, mR, mRl, a);
   kt_end(s);
   MSM_LAUNCH("project_tc_kernel");
 
   if (!fell_back) {
-    // no host round trip: the fix-up reads the queue length on the device
+    // no host round trip: the fix-up reads the queue lengths on the device
     // and reports an overflow in *status (bit 1) for the caller to act on
     kt_begin(KC_PROJECT, s);
-    project_fix_kernel<<<num_sms() * 16, 256, 0, s>>>(X, dtype, n, dim, R,
-                                                      bf16 ? nullptr : (const float*)Bhi, ell,
-                                                      W, xnorm, rnorm, fix, fix_count, fix_cap,
-                                                      strings, recompute, status);
+    project_fix_kernel<<<num_sms() * 16, 256, 0, s>>>(X, dtype, n, dim, Rt, ell, W, xnorm, rnorm,
+                                                      fix, fix_count, fix_cap, dq, dq_count,
+                                                      dq_cap, strings, status);
     kt_end(s);
     MSM_LAUNCH("project_fix_kernel");
+    kt_begin(KC_PROJECT, s);
+    project_fix64_kernel<<<num_sms() * 4, 256, 0, s>>>(X, dtype, n, dim, Rt, ell, W, dq, dq_count,
+                                                       dq_cap, strings, recompute);
+    kt_end(s);
+    MSM_LAUNCH("project_fix64_kernel");
     return MSM_OK;
   }
   // queued bits; an overflowing queue means the tensor-core pass cannot be
@@ -549,17 +711,32 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
     return MSM_OK;
   }
   if (cnt > 0) {
-    int64_t warps = (int64_t)cnt;
+    int64_t warps = ((int64_t)cnt + 3) / 4;
     int grid2 = (int)((warps * 32 + 255) / 256);
     const int cap = num_sms() * 16;
     if (grid2 > cap) grid2 = cap;
     kt_begin(KC_PROJECT, s);
-    project_fix_kernel<<<grid2, 256, 0, s>>>(X, dtype, n, dim, R,
-                                              bf16 ? nullptr : (const float*)Bhi, ell, W, xnorm,
-                                              rnorm, fix, fix_count, fix_cap, strings, recompute,
+    project_fix_kernel<<<grid2, 256, 0, s>>>(X, dtype, n, dim, Rt, ell, W, xnorm, rnorm, fix,
+                                              fix_count, fix_cap, dq, dq_count, dq_cap, strings,
                                               status);
     kt_end(s);
     MSM_LAUNCH("project_fix_kernel");
+    unsigned long long dcnt = 0;
+    MSM_CUDA(cudaMemcpyAsync(&dcnt, dq_count, 8, cudaMemcpyDeviceToHost, s));
+    MSM_CUDA(cudaStreamSynchronize(s));
+    if ((int64_t)dcnt > dq_cap) {
+      *fell_back = true;
+      return MSM_OK;
+    }
+    if (dcnt > 0) {
+      int grid3 = (int)((dcnt + 255) / 256);
+      if (grid3 > cap) grid3 = cap;
+      kt_begin(KC_PROJECT, s);
+      project_fix64_kernel<<<grid3, 256, 0, s>>>(X, dtype, n, dim, Rt, ell, W, dq, dq_count,
+                                                 dq_cap, strings, recompute);
+      kt_end(s);
+      MSM_LAUNCH("project_fix64_kernel");
+    }
   }
   return MSM_OK;
 }

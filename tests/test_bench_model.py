@@ -94,3 +94,12 @@ def test_cpu_oracle_copies_run_and_time_out(bench):
     # an impossible deadline: no result, and the copies are killed
     assert bench.cpu_oracle_copies(X, R, wl, 600, 2, timeout_s=1e-3) is None
     assert bench.usable_cores() >= 1
+
+
+def test_cpu_sample_keeps_the_cluster_size(bench):
+    import workloads as W
+    wl = W.WORKLOADS["scale"]
+    X, nc = bench.cpu_sample_points(wl, wl.n, 2000, 5)
+    assert nc == 2 and X.shape == (2000, wl.dim)   # clusters of 1,000 points, as at 1M
+    X, nc = bench.cpu_sample_points(wl, wl.n, 500, 5)
+    assert nc == 1 and X.shape == (1000, wl.dim)   # never less than one whole cluster
