@@ -579,18 +579,19 @@ def gap_words_mean(k, d):
 
 def int_mix_rate(msm, torch, sm_count, iters=1 << 16):
     """32-bit integer operations per second that the GPU sustains for the
-    pair check's word operation (xor, add, and-not-or), from the library's
-    register-only probe at full occupancy; best of 3 timed launches after a
-    warm-up, CUDA events on the launching stream."""
+    pair check's word operation (xor, add, and-not-or), from the
+    register-only probe (libmsm_probe.so) at full occupancy; best of 3 timed
+    launches after a warm-up, CUDA events on the launching stream."""
+    from paper_0904_3151_gb300 import probe
     blocks = sm_count * 8
     out = torch.empty(blocks * 256 * 8, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
-    msm.int_mix_probe(out, blocks, 1024)
+    probe.int_mix_probe(out, blocks, 1024)
     best = float("inf")
     for _ in range(3):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        msm.int_mix_probe(out, blocks, iters)
+        probe.int_mix_probe(out, blocks, iters)
         e1.record(stream)
         e1.synchronize()
         best = min(best, e0.elapsed_time(e1))
@@ -605,21 +606,34 @@ def kernel_source_hash(kind="pair_check"):
     return h.hexdigest()[:16]
 
 
-def algorithmic(kind, st, n, dim, Q, W_words, passes):
+def algorithmic(kind, st, n, dim, Q, W_words, passes=None):
     """Algorithmic bytes of one launch of `kind` (averaged over its
     launches in the step) -- the per-unit figures are derived in the design
-    notes."""
+    notes.  Grouping of one point set (one batch of all kept-block sets per
+    replicate): the top-digit histogram reads every (string, set) item's
+    string (8 W bytes, from L2: the pool is 8 W n bytes) and writes nothing;
+    the scatter class is the top-digit scatter (writes key + index, 8 bytes)
+    and the bucket sort (reads and writes them, 16 bytes): 24 bytes per item
+    over its two launches."""
     masks = st["masks"] // max(1, Q)
     items = masks * n                      # grouped items per replicate batch
     if kind == "radix_scatter":
-        per_item = (8 * W_words + 8 + (passes - 1) * 16) / passes
-        return items * per_item, "GB/s", "hbm"
+        return items * 24 / 2, "GB/s", "hbm"
     if kind == "radix_hist":
-        per_item = (8 * W_words + (passes - 1) * 4) / passes
-        return items * per_item, "GB/s", "hbm"
+        return items * 8 * W_words, "GB/s", "l2"
     if kind == "recheck":
         return st["cand"] * (8 + 2 * 4 * dim + 12), "GB/s", "hbm"
     return None, None, None
+
+
+def exact_test_ops(k):
+    """Integer operations of the exact tests of one evaluated pair over the
+    field layout (two 16-bit block fields per 32-bit word, ceil(k / 2)
+    words): gap test 3 per word (xor, add, and-not-or), Hamming 3 per word
+    (xor, popc, add) on this replicate and 3 per word on replicate 0, plus 2
+    compares."""
+    words = (k + 1) // 2
+    return 9 * words + 2
 
 
 def traffic_for(kind, workload):
@@ -905,22 +919,30 @@ def main():
     # ---- roofline of the dominant kernel class
     peaks = measured_peaks()
     W_words = (wl.ell + 63) // 64
-    passes = 4
     dom = max(kms, key=lambda k: kms[k]) if kms else None
     roof = None
     hbm_kernels = {}
     for kind in ("radix_scatter", "radix_hist"):
         if klaunch.get(kind):
-            bytes_per_launch, u, bound = algorithmic(kind, st, n, wl.dim, Q, W_words, passes)
+            bytes_per_launch, u, bound = algorithmic(kind, st, n, wl.dim, Q, W_words)
             avg_ms = kms[kind] / klaunch[kind]
             ach = bytes_per_launch / (avg_ms / 1000.0) / 1e9
             hbm_kernels[kind] = {"achieved": ach, "frac": ach / peaks["hbm_gbs"],
-                                 "avg_launch_ms": avg_ms, "launches_per_step": klaunch[kind] // a.steps}
+                                 "avg_launch_ms": avg_ms, "launches_per_step": klaunch[kind] // a.steps,
+                                 "bytes_from": bound}
+    if klaunch.get("radix_scatter") and klaunch.get("radix_hist"):
+        # the whole grouping sort: 24 algorithmic HBM bytes per item over the
+        # histogram, scatter and bucket-sort launches of a replicate
+        per_rep = (st["masks"] // max(1, Q)) * n * 24
+        t = (kms["radix_scatter"] + kms["radix_hist"]) / a.steps / Q
+        hbm_kernels["grouping_sort"] = {"achieved": per_rep / (t / 1000.0) / 1e9,
+                                        "frac": per_rep / (t / 1000.0) / 1e9 / peaks["hbm_gbs"],
+                                        "ms_per_replicate": t}
     if klaunch.get("recheck"):
         # the recheck gathers two rows per candidate, mostly from L2 (X is
         # read ~1 KB per candidate but only 512 MB from DRAM): a gather rate,
         # not an HBM fraction
-        row_bytes, _, _ = algorithmic("recheck", st, n, wl.dim, Q, W_words, passes)
+        row_bytes, _, _ = algorithmic("recheck", st, n, wl.dim, Q, W_words)
         avg_ms = kms["recheck"] / klaunch["recheck"]
         hbm_kernels["recheck_gather"] = {
             "row_bytes_per_s_GB": row_bytes / (avg_ms / 1000.0) / 1e9, "avg_launch_ms": avg_ms,
@@ -932,12 +954,14 @@ def main():
                 "unit": "GB/s", "frac": h["frac"], "traffic": traffic_for(dom, "scale"),
                 "peak_source": peaks["source"]}
     elif dom == "pair_check":
-        # integer-ALU bound: pair inspections per second against the
-        # issue-rate ceiling derived in the design notes
-        # unit: one pair inside a group; algorithmic work per pair in the
-        # field layout = 3 integer ops (xor, add, lop3) per 32-bit word of
-        # fields up to the one holding the highest gap block (mean over the
-        # kept-block sets) + 1 compare
+        # integer-ALU model.  In-group pairs are decided either a row at a
+        # time (the sub-key skip and the reference prefilter) or by the
+        # exact tests (the evaluated pairs).  achieved = in-group pairs
+        # decided per second; peak = the measured integer ceiling divided by
+        # the operations a kernel that tested every in-group pair would need
+        # (3 per field word up to the highest gap block + 1).  The executed
+        # work (evaluated pairs x exact-test operations) is reported against
+        # the same ceiling.
         checks = st["checks"]
         avg_ms = kms[dom] / klaunch[dom]
         per_launch = checks / max(1, klaunch[dom] // a.steps)
@@ -947,6 +971,8 @@ def main():
         nominal_ops = sm_count * 128 * peaks["sm_max_mhz"] * 1e6
         probe_ops = int_mix_rate(msm, torch, sm_count)
         peak = probe_ops / ops_per_check / 1e9
+        ev = st.get("evaluated", 0)
+        ev_ops = ev / max(1, klaunch[dom] // a.steps) * exact_test_ops(wl.k) / (avg_ms / 1000.0)
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "Gpairs/s", "frac": ach / peak, "traffic": traffic_for(dom, "scale"),
                 "peak_source": f"measured: the integer-mix probe (xor, add, and-not-or chains "
@@ -957,10 +983,13 @@ def main():
                                f"to the highest gap block, mean over the kept-block sets, + 1)",
                 "peak_nominal": nominal_ops / ops_per_check / 1e9,
                 "frac_of_nominal": ach / (nominal_ops / ops_per_check / 1e9),
-                "unit_note": "every in-group pair counts, including those the first-gap "
-                             "sub-key decides a tile at a time without per-pair work "
-                             "(about half on the scale geometry), so the integer work "
-                             "executed runs at about half of frac"}
+                "evaluated_share": ev / max(1, checks),
+                "executed_ops_per_s": ev_ops,
+                "executed_frac": ev_ops / probe_ops,
+                "unit_note": "in-group pairs decided per second; most are decided a row at "
+                             "a time (sub-key skip, reference prefilter), evaluated_share "
+                             "take the exact tests (exact_test_ops each), and executed_frac "
+                             "is that integer work against the same measured ceiling"}
     elif dom == "project":
         flops = 2.0 * n * wl.dim * Q * wl.ell
         avg_ms = kms[dom] / klaunch[dom]

@@ -19,7 +19,7 @@ from ._lib import Allocator, Pairs, Params, Stats
 
 __all__ = ["MSMError", "gaussian", "project", "enumerate_pairs", "recheck",
            "eps_graph", "enumerate_sets", "eps_graph_sets", "Plan", "autotune",
-           "eps_count_exhaustive", "int_mix_probe", "collision_p", "miss_bound", "choose_params",
+           "eps_count_exhaustive", "collision_p", "miss_bound", "choose_params",
            "estimate_output",
            "solve_Q", "unpack_pairs", "COSINE", "EUCLIDEAN", "lib"]
 
@@ -444,18 +444,6 @@ def eps_count_exhaustive(X: torch.Tensor, metric, eps: float) -> int:
                                           _metric(metric), ctypes.c_float(eps), ctypes.byref(c),
                                           _stream()), "msm_eps_count_exhaustive")
     return c.value
-
-
-def int_mix_probe(out: torch.Tensor, blocks: int, iters: int, seed: int = 0) -> None:
-    """Launch the integer-mix probe (a measurement aid: the rate of the pair
-    check's xor / add / and-not-or word operation) into `out`, a contiguous
-    int32 CUDA tensor of blocks * 256 * 8 words; asynchronous on the current
-    stream."""
-    assert out.is_cuda and out.is_contiguous() and out.dtype == torch.int32
-    assert out.numel() >= blocks * 256 * 8
-    _check(lib().msm_int_mix_probe(ctypes.c_void_p(out.data_ptr()), blocks, iters,
-                                   ctypes.c_uint32(seed & 0xFFFFFFFF), _stream()),
-           "msm_int_mix_probe")
 
 
 def e2lsh_p(w: float) -> float:

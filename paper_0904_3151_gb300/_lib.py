@@ -134,7 +134,6 @@ SIGNATURES = {
     "msm_mlp_adam": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, vp,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]),
-    "msm_int_mix_probe": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, vp]),
     "msm_eps_count_exhaustive": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_float, i64p, vp]),
 }

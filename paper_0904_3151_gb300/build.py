@@ -2,7 +2,9 @@
 
 Each translation unit under csrc/ is compiled by nvcc in parallel, then
 linked into a shared object against the shared CUDA runtime (so that the
-library and PyTorch use one runtime instance and one current device).
+library and PyTorch use one runtime instance and one current device).  The
+benchmark's measurement aid under probe/ is linked into a library of its own,
+libmsm_probe.so.
 """
 from __future__ import annotations
 
@@ -17,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmsm.so")
+PROBE_SRC = os.path.join(HERE, "probe")
+PROBE_LIB = os.path.join(OUT, "libmsm_probe.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,15 +39,26 @@ def _sources():
     return sorted(glob.glob(os.path.join(SRC, "*.cu")))
 
 
+def _probe_sources():
+    return sorted(glob.glob(os.path.join(PROBE_SRC, "*.cu")))
+
+
 def _deps():
     return _sources() + glob.glob(os.path.join(SRC, "*.cuh")) + [os.path.join(INCLUDE, "msm.h")]
 
 
+def _probe_deps():
+    return _probe_sources() + [os.path.join(INCLUDE, "msm_probe.h")]
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
-        return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(p) <= t for p in _deps())
+    for lib, deps in ((LIB, _deps()), (PROBE_LIB, _probe_deps())):
+        if not os.path.exists(lib):
+            return False
+        t = os.path.getmtime(lib)
+        if not all(os.path.getmtime(p) <= t for p in deps):
+            return False
+    return True
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
@@ -54,7 +69,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        sub = "probe_" if os.path.dirname(src) == PROBE_SRC else ""
+        obj = os.path.join(OUT, sub + os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -63,15 +79,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(r.stderr)
         return obj
 
+    srcs = _sources()
+    psrcs = _probe_sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-           "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+        objs = list(ex.map(compile_one, srcs + psrcs))
+    for lib, part in ((LIB, objs[:len(srcs)]), (PROBE_LIB, objs[len(srcs):])):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *part,
+               "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

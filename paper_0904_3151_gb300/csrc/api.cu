@@ -3,6 +3,7 @@
 //   A0' Gaussian R (Sec. 3.2)          A1  projection + sign (Eq. 3)
 //   A3-A7 blockwise MSM per replicate (Sec. 2.2, Eq. 5, Appendix)
 //   A8  epsilon recheck (Sec. 4.1)     A9  optional canonical order
+#include <nvtx3/nvToolsExt.h>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -244,14 +245,26 @@ static int check_geometry(int64_t n, int ell, int k, int d, int sw = 1) {
 }
 
 // Event-based phase timer (only when stats are requested).
+// Every phase is also an NVTX range ("msm: <phase>"), so a profiler's
+// timeline shows where a call spends its time (a no-op without a tool).
 struct PhaseTimer {
   bool on;
   cudaStream_t s;
   std::vector<cudaEvent_t> ev;
   std::vector<int> phase;
+  bool range_open = false;
   PhaseTimer(bool on_, cudaStream_t s_) : on(on_), s(s_) {}
-  ~PhaseTimer() { for (auto e : ev) cudaEventDestroy(e); }
+  ~PhaseTimer() {
+    if (range_open) nvtxRangePop();
+    for (auto e : ev) cudaEventDestroy(e);
+  }
   void mark(int ph) {  // start of phase ph (-1 = end)
+    static const char* kNames[7] = {"msm: norms and R", "msm: projection",
+                                    "msm: grouping sort", "msm: group boundaries",
+                                    "msm: pair check", "msm: recheck", "msm: canonical order"};
+    if (range_open) nvtxRangePop();
+    range_open = ph >= 0 && ph < 7;
+    if (range_open) nvtxRangePushA(kNames[ph]);
     if (!on) return;
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }

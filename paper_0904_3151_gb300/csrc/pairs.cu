@@ -813,7 +813,8 @@ __device__ __forceinline__ void load_fields(const uint32_t* pool, uint32_t idx,
 // and collected in a per-warp buffer that is appended to E with one atomic
 // when full, so the pairs of consecutive tiles lie together in E (the
 // recheck then finds their rows in L1).
-constexpr int kOut = 64;  // per-warp buffer of pairs for E
+constexpr int kOut = 64;     // per-warp buffer of pairs for E
+constexpr int kQueue = 512;  // per-warp queue of pairs for the exact tests
 
 template <int FP>
 struct WarpStage {
@@ -847,8 +848,8 @@ template <int FP, int FU, bool FUSE, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
 check_fields_kernel(CheckArgs a, const uint32_t* fields) {
   __shared__ __align__(16) WarpStage<FP> stg[kThreads / 32];
-  __shared__ uint64_t sm_q[kThreads / 32][32];       // fused recheck queue
-  __shared__ uint16_t sm_qs[kThreads / 32][1024];    // queued pairs: row << 5 | column
+  __shared__ uint64_t sm_q[FUSE ? kThreads / 32 : 1][32];  // fused recheck queue
+  __shared__ uint16_t sm_qs[kThreads / 32][kQueue];       // queued pairs: row << 5 | column
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpStage<FP>& ws = stg[warp];
   const uint64_t total = *a.total_work;
@@ -938,10 +939,72 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
                    ((K >> (2 * w + 1)) & 1u ? 0x80000000u : 0u);
       }
     }
-    const bool diag = tI == tJ;
+    // Runs of at most 32 members that follow in the batch and lie in the same
+    // grouping are packed into one pass: lanes [O_r, O_r + L_r) hold the
+    // members of run r, and a member pairs only with the later members of
+    // its own run.
+    uint32_t packmask = 1u << t;
+    uint32_t ptotal = tlen;
+    if (!FUSE && tlen <= (uint32_t)kSmall) {
+      while (lv) {
+        const int t2 = __ffs(lv) - 1;
+        const uint32_t l2 = __shfl_sync(0xffffffffu, len, t2);
+        const uint32_t s2 = __shfl_sync(0xffffffffu, st, t2);
+        if (l2 > (uint32_t)kSmall || ptotal + l2 > 32u || (int)(s2 / a.n) != seg) break;
+        ptotal += l2;
+        packmask |= 1u << t2;
+        lv &= lv - 1;
+      }
+    }
+    bool diag;
+    uint32_t cand;
+    __syncwarp();  // the previous item's queue stage is done with the stage
+    if (__popc(packmask) > 1) {
+      diag = true;
+      // offsets of the packed runs: prefix of their lengths over the batch lanes
+      const uint32_t mylen = (packmask >> lane) & 1u ? len : 0u;
+      uint32_t inc = mylen;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      uint32_t mst = 0, mend = 0;  // this lane's member position and run end lane
+      for (uint32_t pm = packmask; pm; pm &= pm - 1) {
+        const int t2 = __ffs(pm) - 1;
+        const uint32_t e2 = __shfl_sync(0xffffffffu, inc, t2);
+        const uint32_t l2 = __shfl_sync(0xffffffffu, len, t2);
+        const uint32_t s2 = __shfl_sync(0xffffffffu, st, t2);
+        const uint32_t o2 = e2 - l2;
+        if ((uint32_t)lane >= o2 && (uint32_t)lane < e2) {
+          mst = s2 + ((uint32_t)lane - o2);
+          mend = e2;
+        }
+      }
+      const bool vm = (uint32_t)lane < ptotal;
+      uint32_t f[FP], f0[FP];
+      uint32_t ic = 0;
+#pragma unroll
+      for (int w = 0; w < FP; ++w) f[w] = f0[w] = 0;
+      if (vm) {
+        ic = a.vals[mst];
+        load_fields<FP>(pool, ic, f);
+        if (rep0) load_fields<FP>(pool0, ic, f0);
+      }
+#pragma unroll
+      for (int w = 0; w < FP; ++w) {
+        ws.cf[lane][w] = f[w];
+        ws.cf0[lane][w] = f0[w];
+      }
+      ws.ci[lane] = ic;
+      cand = vm ? (((mend == 32u ? 0u : (1u << mend)) - 1u) & ~((2u << lane) - 1u)) : 0u;
+      if (lane == 31) cand = 0u;
+      cache_g = 0xffffffffu;  // the stage no longer holds a column block
+      __syncwarp();
+    } else {
+    diag = tI == tJ;
     const uint32_t ncols = min(32u, tlen - tJ * 32);
     const bool pf = tlen > 8;  // tiny runs have too few pairs for the prefilter
-    __syncwarp();  // the previous item's queue stage is done with the stage
     if (tg != cache_g || tJ != cache_J) {
       // stage the column block, its references and masks
       const uint32_t cb = tJ * 32 + lane;
@@ -1011,7 +1074,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
       }
       ws.ri[lane] = ia;
     }
-    uint32_t cand = va ? (ncols == 32 ? 0xffffffffu : ((1u << ncols) - 1u)) : 0u;
+    cand = va ? (ncols == 32 ? 0xffffffffu : ((1u << ncols) - 1u)) : 0u;
     if (diag) cand &= lane == 31 ? 0u : (0xffffffffu << (lane + 1));
     if (pf) {
 #pragma unroll
@@ -1024,7 +1087,15 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
         }
       }
     }
-    const uint32_t cnt2 = __popc(cand);
+    }  // tile
+    const uint32_t nall = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(cand));
+    if (nall == 0) continue;
+    // the queue holds kQueue pairs: a tile with more is queued in two halves
+    // of 16 rows (at most 512 pairs each)
+    const int nparts = nall > (uint32_t)kQueue ? 2 : 1;
+    for (int part = 0; part < nparts; ++part) {
+    const uint32_t cpart = (nparts == 1 || (lane >> 4) == part) ? cand : 0u;
+    const uint32_t cnt2 = __popc(cpart);
     uint32_t incl = cnt2;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1033,8 +1104,9 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
     }
     const uint32_t nq = __shfl_sync(0xffffffffu, incl, 31);
     if (nq == 0) continue;
+    __syncwarp();  // the previous part's queue entries have been read
     {
-      uint32_t m = cand, pos = incl - cnt2;
+      uint32_t m = cpart, pos = incl - cnt2;
       while (m) {
         const int c = __ffs(m) - 1;
         m &= m - 1;
@@ -1101,6 +1173,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
         nout += npass;
       }
     }
+    }  // parts
     }
   }
   }

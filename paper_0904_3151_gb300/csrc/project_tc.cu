@@ -53,7 +53,8 @@ constexpr int kEpiWarps = 8;        // warp w: TMEM lanes (rows) 32 (w % 4) ..,
                                     // columns 32 (w / 4) .. of each tile
 constexpr int kTcThreads = (kEpiWarps + 2) * 32;  // + TMA warp + MMA warp
 constexpr uint32_t kDrainPolls = 1u << 24;
-constexpr size_t kSmemBudget = 200 * 1024;
+constexpr int kFixBuf = 64;         // undecided bits buffered per epilogue warp
+constexpr size_t kSmemBudget = 200 * 1024 - 8 * kEpiWarps * kFixBuf;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -183,6 +184,20 @@ struct TcArgs {
   unsigned* status;    // bit 0: a bounded wait gave up
 };
 
+// Appends a warp's buffered undecided bits to the fix-up queue (one atomic).
+__device__ __forceinline__ void flush_fix(const TcArgs& a, const uint64_t* qbuf, uint32_t& nq,
+                                          int lane) {
+  if (!nq) return;
+  __syncwarp();
+  unsigned long long b = 0;
+  if (lane == 0) b = atomicAdd(a.fix_count, (unsigned long long)nq);
+  b = __shfl_sync(0xffffffffu, b, 0);
+  for (uint32_t t = lane; t < nq; t += 32)
+    if ((int64_t)(b + t) < a.fix_cap) a.fix[b + t] = qbuf[t];
+  __syncwarp();
+  nq = 0;
+}
+
 // 320 threads: warps 0-7 epilogue (warp 0 also allocates TMEM), warp 8 lane
 // 0 issues the TMA copies, warp 9 lane 0 the MMAs.
 template <bool XLO>
@@ -206,6 +221,7 @@ project_tc_kernel(const __grid_constant__ CUtensorMap tmX,
   uint64_t* tempty = tfull + 2;
   uint32_t* tslot = (uint32_t*)(tempty + 2);
   uint32_t* abortf = tslot + 1;
+  uint64_t* fixbuf = (uint64_t*)(tslot + 4);  // [kEpiWarps][kFixBuf]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row0 = (int64_t)blockIdx.x * kRows;
@@ -331,6 +347,8 @@ project_tc_kernel(const __grid_constant__ CUtensorMap tmX,
     const int colsPerRep = a.W * 64;
     const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
     uint32_t* strings32 = reinterpret_cast<uint32_t*>(a.strings);
+    uint64_t* qbuf = fixbuf + warp * kFixBuf;  // this warp's undecided bits
+    uint32_t nq = 0;                           // entries in qbuf (warp-uniform)
     for (int t = 0; t < a.ctiles; ++t) {
       const int b = t & 1;
       const uint32_t bp = (uint32_t)((t >> 1) & 1);
@@ -364,7 +382,7 @@ project_tc_kernel(const __grid_constant__ CUtensorMap tmX,
           else if (tv > 0.f) bits |= 1u << j;
         }
       }
-      // queue the undecided bits: one atomic per warp
+      // collect the undecided bits in the warp's buffer
       uint32_t cnt = __popc(flagged), incl = cnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -373,20 +391,27 @@ project_tc_kernel(const __grid_constant__ CUtensorMap tmX,
       }
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
       if (total) {
-        unsigned long long b0 = 0;
-        if (lane == 31) b0 = atomicAdd(a.fix_count, (unsigned long long)total);
-        b0 = __shfl_sync(0xffffffffu, b0, 31) + (incl - cnt);
+        if (nq + total > (uint32_t)kFixBuf) flush_fix(a, qbuf, nq, lane);
+        uint32_t pos = nq + incl - cnt;
         while (flagged) {
           const int j = __ffs(flagged) - 1;
           flagged &= flagged - 1;
-          if ((int64_t)b0 < a.fix_cap)
-            a.fix[b0] = ((uint64_t)row << 32) | (uint32_t)(q * a.ell + cw + j);
-          ++b0;
+          const uint64_t e = ((uint64_t)row << 32) | (uint32_t)(q * a.ell + cw + j);
+          if (pos < (uint32_t)kFixBuf) {
+            qbuf[pos] = e;
+          } else {  // more than a buffer's worth in one tile: append directly
+            const unsigned long long b0 = atomicAdd(a.fix_count, 1ull);
+            if ((int64_t)b0 < a.fix_cap) a.fix[b0] = e;
+          }
+          ++pos;
         }
+        nq = min(nq + total, (uint32_t)kFixBuf);
+        __syncwarp();
       }
       // the low (half 0) or high (half 1) 32 bits of the word, little-endian
       if (live) strings32[(((size_t)q * a.n + row) * a.W + cw / 64) * 2 + half] = bits;
     }
+    flush_fix(a, qbuf, nq, lane);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -671,9 +696,11 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
   a.fix_count = fix_count;
   a.status = status;
 
-  // X tile (high [+ low]) + the ring of R tiles (high + low) + barriers
+  // X tile (high [+ low]) + the ring of R tiles (high + low) + barriers +
+  // the epilogue warps' buffers of undecided bits
   const size_t smem = 1024 + (size_t)(xlo ? 2 : 1) * a.chunks * kXBox +
-                      (size_t)a.stages * 2 * a.chunks * kRBox + 8 * (1 + 2 * kMaxStages + 4) + 64;
+                      (size_t)a.stages * 2 * a.chunks * kRBox + 8 * (1 + 2 * kMaxStages + 4) + 16 +
+                      8 * (size_t)kEpiWarps * kFixBuf;
   auto kern = xlo ? project_tc_kernel<true> : project_tc_kernel<false>;
   MSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned grid = (unsigned)((n + kRows - 1) / kRows);

@@ -9,9 +9,14 @@
 // SM's integer pipes sustain for the mix.  The chains feed each round's sum
 // back as the next round's `a`, which keeps the compiler from hoisting or
 // folding any of the three operations.
-#include "msm_internal.cuh"
+//
+// Built as its own library (libmsm_probe.so, declared in msm_probe.h) for
+// the benchmark: the method's library does not carry it.
+#include <cuda_runtime.h>
+#include <stdint.h>
 
-namespace msm {
+#include "../../include/msm_probe.h"
+
 namespace {
 
 constexpr int kProbeThreads = 256;
@@ -42,15 +47,10 @@ int_mix_kernel(uint32_t* out, int iters, uint32_t seed) {
 }
 
 }  // namespace
-}  // namespace msm
-
-using namespace msm;
 
 extern "C" int msm_int_mix_probe(uint32_t* out, int blocks, int iters, uint32_t seed,
                                  void* stream) {
-  if (!out || blocks < 1 || iters < 0)
-    return set_error("invalid msm_int_mix_probe arguments"), MSM_E_INVAL;
+  if (!out || blocks < 1 || iters < 0) return -1;
   int_mix_kernel<<<blocks, kProbeThreads, 0, (cudaStream_t)stream>>>(out, iters, seed);
-  MSM_LAUNCH("int_mix_kernel");
-  return MSM_OK;
+  return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }

@@ -21,8 +21,8 @@ def L():
     return msm.lib()
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "msm.h")).read()
+def _declared(header="msm.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return set(re.findall(r"^\s*(?:int|int64_t|double|void\*?|const char\*)\s+(msm_\w+)\s*\(", src,
                           flags=re.M))
@@ -35,6 +35,19 @@ def test_every_declared_symbol_is_exported(L):
     for nm in sorted(names):
         assert hasattr(L, nm), nm
     assert names == set(_lib.SIGNATURES), names ^ set(_lib.SIGNATURES)
+
+
+def test_probe_library_is_separate(L):
+    """The measurement aid lives in libmsm_probe.so, not in the method's
+    library."""
+    import ctypes
+    from paper_0904_3151_gb300 import build as b
+    names = _declared("msm_probe.h")
+    assert names == {"msm_int_mix_probe"}
+    P = ctypes.CDLL(b.PROBE_LIB)
+    for nm in names:
+        assert hasattr(P, nm)
+        assert not hasattr(L, nm)
 
 
 def test_version_and_strerror(L):

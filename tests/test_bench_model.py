@@ -38,23 +38,29 @@ def test_gap_words_bounds(bench):
 
 def test_algorithmic_bytes_hand_counts(bench):
     # one replicate batch of the scale workload: 210 kept sets x n items,
-    # strings of W = 2 words, 4 radix passes of 8-bit digits over 32-bit keys
+    # strings of W = 2 words, one point set (top-digit pass + bucket sort)
     st = {"masks": 12 * 210, "cand": 1000}
     n = 1000
     items = 210 * n
-    # scatter: pass 0 reads the 16-byte string and writes key + index (8 B),
-    # passes 1-3 read and write key + index (16 B): (16 + 8 + 48) / 4 = 18 B
-    b, unit, bound = bench.algorithmic("radix_scatter", st, n, 128, 12, 2, 4)
-    assert (b, unit, bound) == (items * 18, "GB/s", "hbm")
-    # histogram: pass 0 reads the string (16 B), passes 1-3 the key (4 B):
-    # (16 + 12) / 4 = 7 B
-    b, _, _ = bench.algorithmic("radix_hist", st, n, 128, 12, 2, 4)
-    assert b == items * 7
+    # scatter class, two launches per replicate: the top-digit scatter writes
+    # key + index (8 B), the bucket sort reads and writes them (16 B)
+    b, unit, bound = bench.algorithmic("radix_scatter", st, n, 128, 12, 2)
+    assert (b, unit, bound) == (items * 24 / 2, "GB/s", "hbm")
+    # histogram: reads the 16-byte string of every item (from L2)
+    b, _, bound = bench.algorithmic("radix_hist", st, n, 128, 12, 2)
+    assert (b, bound) == (items * 16, "l2")
     # recheck: the pair (8 B), two float rows of 128 (1024 B), pair and
     # distance out (12 B)
-    b, _, _ = bench.algorithmic("recheck", st, n, 128, 12, 2, 4)
+    b, _, _ = bench.algorithmic("recheck", st, n, 128, 12, 2)
     assert b == 1000 * (8 + 1024 + 12)
-    assert bench.algorithmic("pair_check", st, n, 128, 12, 2, 4) == (None, None, None)
+    assert bench.algorithmic("pair_check", st, n, 128, 12, 2) == (None, None, None)
+
+
+def test_exact_test_ops_hand_count(bench):
+    # k = 10 blocks: 5 field words; per word 3 (gap) + 3 (Hamming) + 3
+    # (replicate-0 Hamming), plus 2 compares
+    assert bench.exact_test_ops(10) == 47
+    assert bench.exact_test_ops(8) == 38
 
 
 def test_clock_samples_summary(bench):

@@ -38,7 +38,8 @@ def _probe_numpy(blocks, iters, seed):
 def test_int_mix_probe_matches_numpy(msm, blocks, iters, seed):
     import torch
     out = torch.full((blocks * 256 * 8,), -1, dtype=torch.int32, device="cuda")
-    msm.int_mix_probe(out, blocks, iters, seed)
+    from paper_0904_3151_gb300 import probe
+    probe.int_mix_probe(out, blocks, iters, seed)
     torch.cuda.synchronize()
     got = out.cpu().numpy().view(np.uint32)
     assert np.array_equal(got, _probe_numpy(blocks, iters, seed))
@@ -46,4 +47,5 @@ def test_int_mix_probe_matches_numpy(msm, blocks, iters, seed):
 
 def test_int_mix_probe_rejects_bad_arguments(msm):
     import ctypes
-    assert msm.lib().msm_int_mix_probe(None, 1, 1, ctypes.c_uint32(0), None) == -1
+    from paper_0904_3151_gb300 import probe
+    assert probe.load().msm_int_mix_probe(None, 1, 1, ctypes.c_uint32(0), None) == -1
