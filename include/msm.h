@@ -420,7 +420,13 @@ int msm_autotune(const void* X, const int64_t* set_offsets, int nsets,
  * Parameter vector order (float): W1, b1, W2, b2. */
 
 /* y for every row of X (device [n][dim] of dtype) into device Y
- * [n][dim_out].  Scratch from cudaMallocAsync.  Asynchronous. */
+ * [n][dim_out].  On tcgen05 tensor cores, both layers fused, when dim <= 128
+ * (multiple of 8), hidden is a multiple of 64 and dim_out is 64 or 128: X
+ * (float) and the gelu activations are then split into bf16 high and low
+ * parts, so every operand carries 16 significant bits and every product
+ * accumulates in float; other shapes use a float CUDA-core GEMM.  Scratch
+ * from cudaMallocAsync.  Synchronises (tensor-core path: it reads the
+ * status of its bounded waits and returns MSM_E_TIMEOUT if one ran out). */
 int msm_mlp_forward(const void* X, int64_t n, int dim, int dtype,
                     const void* W1, const float* b1, const void* W2,
                     const float* b2, int hidden, int dim_out, float* Y,

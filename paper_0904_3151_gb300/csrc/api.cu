@@ -1240,6 +1240,21 @@ int msm_mlp_forward(const void* X, int64_t n, int dim, int dtype, const void* W1
       dim_out < 1 || (dtype != MSM_DT_F32 && dtype != MSM_DT_BF16))
     return set_error("invalid msm_mlp_forward arguments"), MSM_E_INVAL;
   Scratch sc(nullptr, s);
+  if (mlp_tc_supported(dtype, dim, hidden, dim_out, (uintptr_t)X)) {
+    // tensor cores, both layers fused; rows in chunks of 2^20 (the split
+    // copy of float X is the chunk's scratch)
+    const int64_t chunk = n < (1 << 20) ? n : (1 << 20);
+    void* ws = sc.get(mlp_tc_scratch_bytes(chunk, dim, dtype));
+    if (!ws) return MSM_E_NOMEM;
+    const size_t es = dtype == MSM_DT_BF16 ? 2 : 4;
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+      const int64_t rows = (n - r0) < chunk ? (n - r0) : chunk;
+      const int rc = launch_mlp_tc((const char*)X + (size_t)r0 * dim * es, dtype, rows, dim, W1, b1,
+                                   W2, b2, hidden, dim_out, Y + (size_t)r0 * dim_out, ws, s);
+      if (rc) return rc;
+    }
+    return MSM_OK;
+  }
   const int64_t chunk = n < (1 << 18) ? n : (1 << 18);
   float* H = (float*)sc.get(4 * (size_t)chunk * hidden);
   float* A = (float*)sc.get(4 * (size_t)chunk * hidden);

@@ -153,6 +153,16 @@ bool tc_project_supported(int dtype, int dim, uintptr_t xaddr);
 // Poll limit of the projection's bounded waits (0: the default); returns
 // the previous limit.
 int set_wait_polls(uint32_t polls);
+uint32_t wait_polls();
+
+// mlp_tc.cu: the learned projection's feature map on tcgen05 (both layers
+// fused per 128 rows); ws: mlp_tc_scratch_bytes.  Synchronises (reads the
+// status of its bounded waits).
+bool mlp_tc_supported(int dtype, int dim, int hidden, int dim_out, uintptr_t xaddr);
+size_t mlp_tc_scratch_bytes(int64_t n, int dim, int dtype);
+int launch_mlp_tc(const void* X, int dtype, int64_t n, int dim, const void* W1,
+                  const float* b1, const void* W2, const float* b2, int hidden, int dim_out,
+                  float* Y, void* ws, cudaStream_t s);
 size_t tc_project_scratch_bytes(int64_t n, int dim, int Q, int ell, int dtype);
 // *fell_back = true when the queue overflowed (the caller must then run the
 // SIMT projection, which overwrites every string).  fell_back == NULL: no
