@@ -827,6 +827,7 @@ struct WarpStage {
   uint32_t ref[kMaxFieldBlocks];    // reference value per gap block
   uint32_t colat[kMaxFieldBlocks];  // columns at the reference
   uint64_t out[kOut];               // pairs waiting to be appended to E
+  uint64_t def[32];                 // pairs waiting for the test of replicates 1 .. q-1
 };
 
 // Appends the warp's buffered pairs to E (one atomic).
@@ -842,6 +843,37 @@ __device__ __forceinline__ void flush_out(const CheckArgs& a, WarpStage<FP>& ws,
     if (b + t < (unsigned long long)a.cap) a.cand[b + t] = ws.out[t];
   __syncwarp();
   nout = 0;
+}
+
+// Replicate test of the deferred pairs ws.def[0 .. ndef), one per lane.  A
+// pair that passed every test of this replicate and differs by more than d in
+// replicate 0 still has to differ by more than d in replicates 1 .. q-1,
+// whose fields are read from global memory (they do not fit in L2).  Few
+// pairs get this far (about one in 30 at the scale workload), so testing
+// them one batch at a time made nearly every batch of 32 wait for a DRAM
+// round trip; collected 32 at a time, a warp waits once per 32 such pairs.
+// Passing pairs join the E buffer.  (The count-only form tests them in
+// place: its distance evaluation follows each batch.)
+template <int FP>
+__device__ __forceinline__ void flush_deferred(const CheckArgs& a, const uint32_t* fields,
+                                               WarpStage<FP>& ws, uint32_t& ndef,
+                                               uint32_t& nout, int lane) {
+  if (!ndef) return;
+  __syncwarp();
+  bool ok = false;
+  uint64_t pr = 0;
+  if ((uint32_t)lane < ndef) {
+    pr = ws.def[lane];
+    ok = replicates_ok_fields<FP>(a, fields, (uint32_t)(pr >> 32), (uint32_t)pr, 1);
+  }
+  ndef = 0;
+  __syncwarp();
+  const unsigned bal = __ballot_sync(0xffffffffu, ok);
+  if (!bal) return;
+  if (nout + __popc(bal) > (uint32_t)kOut) flush_out<FP>(a, ws, nout, lane);
+  if (ok) ws.out[nout + __popc(bal & ((1u << lane) - 1u))] = pr;
+  nout += __popc(bal);
+  __syncwarp();
 }
 
 template <int FP, int FU, bool FUSE, int MINB>
@@ -870,6 +902,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
   for (int w = 0; w < FP; ++w) gapf[w] = keepf[w] = 0;
   uint32_t cache_g = 0xffffffffu, cache_J = 0;  // column block held in ws
   uint32_t nout = 0;                            // pairs in ws.out (warp-uniform)
+  uint32_t ndef = 0;                            // pairs in ws.def (warp-uniform)
   unsigned long long evaluated = 0;             // queued pairs (warp-uniform)
   for (;;) {  // dynamic chunks of work items
   unsigned chunk = 0;
@@ -1122,7 +1155,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
     for (uint32_t b0 = 0; b0 < nq; b0 += 32) {
       __syncwarp();
       const uint32_t nb = min(32u, nq - b0);
-      bool ok = false;
+      bool ok = false, later = false;
       uint32_t ii = 0, jj = 0, e = 0;
       if ((uint32_t)lane < nb) {
         e = sm_qs[warp][b0 + lane];
@@ -1139,10 +1172,22 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
             int h = 0;
 #pragma unroll
             for (int w = 0; w < FU; ++w) h += __popc(sym_diff32(rowf0[r][w] ^ ws.cf0[c][w], a.sw));
-            ok = h > a.d && replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj,
-                                                     ii < jj ? jj : ii, 1);
+            if constexpr (FUSE) {
+              ok = h > a.d && replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj,
+                                                       ii < jj ? jj : ii, 1);
+            } else {  // replicates 1 .. q-1 are tested later, 32 pairs at a time
+              later = h > a.d && a.q > 1;
+              ok = h > a.d && a.q == 1;
+            }
           }
         }
+      }
+      const unsigned dbal = __ballot_sync(0xffffffffu, later);
+      if (!FUSE && dbal) {
+        if (ndef + __popc(dbal) > 32u) flush_deferred<FP>(a, fields, ws, ndef, nout, lane);
+        if (later) ws.def[ndef + __popc(dbal & ((1u << lane) - 1u))] = ordered_pair(ii, jj);
+        ndef += __popc(dbal);
+        __syncwarp();
       }
       if constexpr (FUSE) {
         fuse_one(a, ok, ii, jj, lane, sm_q[warp], acc);
@@ -1177,8 +1222,12 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
     }
   }
   }
-  if (!FUSE) flush_out<FP>(a, ws, nout, lane);
-  if constexpr (FUSE) fuse_finish(a, acc, lane);
+  if constexpr (!FUSE) {
+    flush_deferred<FP>(a, fields, ws, ndef, nout, lane);
+    flush_out<FP>(a, ws, nout, lane);
+  } else {
+    fuse_finish(a, acc, lane);
+  }
   if (lane == 0 && evaluated && a.evaluated) atomicAdd(a.evaluated, evaluated);
 }
 
