@@ -357,7 +357,7 @@ __device__ __forceinline__ void fuse_eval(const CheckArgs& a, const uint64_t* q,
     const bool valid = slot < nb;
     const uint64_t pr = valid ? q[slot] : 0ull;
     const int64_t i = (int64_t)(pr >> 32), j = (int64_t)(pr & 0xffffffffu);
-    const float S = dist::group_sq_dist<4>(a.X, a.dtype, i, j, a.dim, sl);
+    const float S = dist::group_sq_dist<4, false>(a.X, a.dtype, i, j, a.dim, sl);
     bool keep = false;
     if (valid && sl == 0) {
       const float ni = a.metric == MSM_COSINE ? a.nrm[i] : 0.f;
@@ -1412,7 +1412,7 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   a.dim = b.dim;
   a.metric = b.metric;
   a.eps = b.eps;
-  a.relS = 10.f * (float)dist::kU;
+  a.relS = dist::sq_dist_rel(b.dim, 4, false);
   a.nrm = b.nrm;
   a.kept = b.kept;
   a.set_kept = b.set_kept;

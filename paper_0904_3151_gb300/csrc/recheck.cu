@@ -40,8 +40,10 @@ recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
     if (lane_id() == 0) b0 = atomicAdd(count, (unsigned long long)ns);
     b0 = __shfl_sync(0xffffffffu, b0, 0);
     for (uint32_t q = lane_id(); q < ns; q += 32) {
-      if (pairs_out) pairs_out[b0 + q] = st_p[wb][q];
-      if (dist_out) dist_out[b0 + q] = st_d[wb][q];
+      if (pairs_out)
+        __stcs(reinterpret_cast<unsigned long long*>(pairs_out) + b0 + q,
+               (unsigned long long)st_p[wb][q]);
+      if (dist_out) __stcs(dist_out + b0 + q, st_d[wb][q]);
     }
     __syncwarp();
     ns = 0;
@@ -56,7 +58,9 @@ recheck_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
   for (int64_t base = c0 + (threadIdx.x >> 5) * (32 / G); base < c1; base += kPerIter) {
     const int64_t t = base + grp;
     const bool in_range = t < c1;
-    const uint64_t pr = in_range ? cand[t] : 0;
+    // E and the output stream through once: kept out of L2's way of the rows
+    const uint64_t pr =
+        in_range ? __ldcs(reinterpret_cast<const unsigned long long*>(cand) + t) : 0ull;
     const int64_t i = (int64_t)(pr >> 32), j = (int64_t)(pr & 0xffffffffu);
     const bool valid = in_range && i < j && j < n;
     if (in_range && !valid && sl == 0 && bad) atomicOr(bad, 1u);
@@ -165,7 +169,7 @@ int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
   int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
   const int64_t cap = (int64_t)num_sms() * kCtasPerSm;
   if (grid > cap) grid = cap;
-  const float relS = 10.f * (float)kU;
+  const float relS = sq_dist_rel(dim, 4);
   kt_begin(KC_RECHECK, s);
   recheck_kernel<<<(int)grid, kThreads, 0, s>>>(X, dtype, n, dim, metric, eps, nrm, cand,
                                                 m_dev, m_max, pairs_out, dist_out,
