@@ -1169,7 +1169,23 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
     const uint32_t nq = __shfl_sync(0xffffffffu, incl, 31);
     if (nq == 0) continue;
     __syncwarp();  // the previous part's queue entries have been read
-    {
+    // Queue entries row << 5 | column in row-major order.  A lane writing its
+    // own row's entries one at a time takes as many steps as the fullest row;
+    // the warp writing one row at a time (each lane its column) takes as
+    // many as there are rows with entries.  Whichever is shorter; both give
+    // the same queue.
+    const uint32_t qrows = __ballot_sync(0xffffffffu, cpart != 0u);
+    if (__popc(qrows) < __reduce_max_sync(0xffffffffu, cnt2)) {
+      uint32_t pos = 0;
+      for (uint32_t rr = qrows; rr; rr &= rr - 1) {
+        const int r = __ffs(rr) - 1;
+        const uint32_t cr = __shfl_sync(0xffffffffu, cpart, r);
+        if ((cr >> lane) & 1u)
+          sm_qs[warp][pos + __popc(cr & ((1u << lane) - 1u))] =
+              (uint16_t)(((uint32_t)r << 5) | (uint32_t)lane);
+        pos += __popc(cr);
+      }
+    } else {
       uint32_t m = cpart, pos = incl - cnt2;
       while (m) {
         const int c = __ffs(m) - 1;
