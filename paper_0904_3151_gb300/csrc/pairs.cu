@@ -1198,10 +1198,38 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
     const uint32_t (*rowf)[FP] = diag ? ws.cf : ws.rf;
     const uint32_t (*rowf0)[FP] = diag ? ws.cf0 : ws.rf0;
     const uint32_t* rowi = diag ? ws.ci : ws.ri;
+    // In a later replicate most queued pairs were already within d in
+    // replicate 0 (Appendix, first trick) and are rejected there: that test
+    // runs first over the whole queue, whose survivors are compacted in place
+    // (a round writes only entries already read), so the other tests run on
+    // a few full batches instead of on every batch.
+    uint32_t nq1 = nq;
+    if (rep0) {
+      uint32_t n1 = 0;
+      for (uint32_t b0 = 0; b0 < nq; b0 += 32) {
+        __syncwarp();
+        const uint32_t nb = min(32u, nq - b0);
+        bool keep = false;
+        uint32_t e = 0;
+        if ((uint32_t)lane < nb) {
+          e = sm_qs[warp][b0 + lane];
+          const uint32_t r = e >> 5, c = e & 31u;
+          int h = 0;
+#pragma unroll
+          for (int w = 0; w < FU; ++w) h += __popc(sym_diff32(rowf0[r][w] ^ ws.cf0[c][w], a.sw));
+          keep = h > a.d;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) sm_qs[warp][n1 + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)e;
+        n1 += __popc(bal);
+      }
+      nq1 = n1;
+    }
     uint32_t npass = 0;
-    for (uint32_t b0 = 0; b0 < nq; b0 += 32) {
+    for (uint32_t b0 = 0; b0 < nq1; b0 += 32) {
       __syncwarp();
-      const uint32_t nb = min(32u, nq - b0);
+      const uint32_t nb = min(32u, nq1 - b0);
       bool ok = false, later = false;
       uint32_t ii = 0, jj = 0, e = 0;
       if ((uint32_t)lane < nb) {
@@ -1214,18 +1242,12 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
             fields_rest_ok<FP, FU>(fr, ws.cf[c], a.d, a.sw, hashed, keepf)) {
           ii = rowi[r];
           jj = ws.ci[c];
-          ok = true;
-          if (rep0) {
-            int h = 0;
-#pragma unroll
-            for (int w = 0; w < FU; ++w) h += __popc(sym_diff32(rowf0[r][w] ^ ws.cf0[c][w], a.sw));
-            if constexpr (FUSE) {
-              ok = h > a.d && replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj,
-                                                       ii < jj ? jj : ii, 1);
-            } else {  // replicates 1 .. q-1 are tested later, 32 pairs at a time
-              later = h > a.d && a.q > 1;
-              ok = h > a.d && a.q == 1;
-            }
+          if constexpr (FUSE) {  // replicates 1 .. q-1 in place
+            ok = !rep0 || replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj,
+                                                   ii < jj ? jj : ii, 1);
+          } else {  // replicates 1 .. q-1 are tested later, 32 pairs at a time
+            later = a.q > 1;
+            ok = a.q <= 1;
           }
         }
       }
