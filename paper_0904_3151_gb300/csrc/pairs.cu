@@ -288,6 +288,13 @@ __device__ __forceinline__ uint32_t sym_diff32(uint32_t x, int sw) {
   if (sw == 4) return (x | (x >> 1) | (x >> 2) | (x >> 3)) & 0x11111111u;
   return x;
 }
+// sym_diff32 with the symbol width fixed at compile time when SW = 1 (sign
+// bits: every bit is a symbol), else read at run time.
+template <int SW>
+__device__ __forceinline__ uint32_t symd32(uint32_t x, int sw) {
+  if constexpr (SW == 1) return x;
+  else return sym_diff32(x, sw);
+}
 __device__ __forceinline__ uint64_t sym_diff64(uint64_t x, int sw) {
   if (sw == 2) return (x | (x >> 1)) & 0x5555555555555555ull;
   if (sw == 4) return (x | (x >> 1) | (x >> 2) | (x >> 3)) & 0x1111111111111111ull;
@@ -737,7 +744,7 @@ __device__ __forceinline__ bool gaps_differ(const uint32_t (&fa)[FP],
 
 // Hamming (differing symbols) <= d and (hashed keys only) all kept fields
 // equal.
-template <int FP, int FU>
+template <int FP, int FU, int SW>
 __device__ __forceinline__ bool fields_rest_ok(const uint32_t (&fa)[FP],
                                                const uint32_t* fb, int d, int sw,
                                                bool hashed,
@@ -747,14 +754,14 @@ __device__ __forceinline__ bool fields_rest_ok(const uint32_t (&fa)[FP],
 #pragma unroll
   for (int w = 0; w < FU; ++w) {
     const uint32_t x = fa[w] ^ fb[w];
-    h += __popc(sym_diff32(x, sw));
+    h += __popc(symd32<SW>(x, sw));
     bad |= keepf[w] & ((x + 0x7FFF7FFFu) & 0x80008000u);
   }
   return h <= d && (!hashed || bad == 0);
 }
 
 // No replicate g0 <= g < q has the pair within d (Appendix, first trick).
-template <int FP>
+template <int FP, int SW>
 __device__ __forceinline__ bool replicates_ok_fields(const CheckArgs& a,
                                                      const uint32_t* fields,
                                                      uint32_t i, uint32_t j, int g0 = 0) {
@@ -765,7 +772,7 @@ __device__ __forceinline__ bool replicates_ok_fields(const CheckArgs& a,
 #pragma unroll
     for (int w = 0; w < FP / 2; ++w) {
       const uint2 p = __ldg(fi + w), q2 = __ldg(fj + w);
-      h += __popc(sym_diff32(p.x ^ q2.x, a.sw)) + __popc(sym_diff32(p.y ^ q2.y, a.sw));
+      h += __popc(symd32<SW>(p.x ^ q2.x, a.sw)) + __popc(symd32<SW>(p.y ^ q2.y, a.sw));
     }
     if (h <= a.d) return false;
   }
@@ -882,7 +889,7 @@ __device__ __forceinline__ uint32_t gap_peers(const uint32_t (&f)[FP], uint32_t 
 // round trip; collected 32 at a time, a warp waits once per 32 such pairs.
 // Passing pairs join the E buffer.  (The count-only form tests them in
 // place: its distance evaluation follows each batch.)
-template <int FP>
+template <int FP, int SW>
 __device__ __forceinline__ void flush_deferred(const CheckArgs& a, const uint32_t* fields,
                                                WarpStage<FP>& ws, uint32_t& ndef,
                                                uint32_t& nout, int lane) {
@@ -892,7 +899,7 @@ __device__ __forceinline__ void flush_deferred(const CheckArgs& a, const uint32_
   uint64_t pr = 0;
   if ((uint32_t)lane < ndef) {
     pr = ws.def[lane];
-    ok = replicates_ok_fields<FP>(a, fields, (uint32_t)(pr >> 32), (uint32_t)pr, 1);
+    ok = replicates_ok_fields<FP, SW>(a, fields, (uint32_t)(pr >> 32), (uint32_t)pr, 1);
   }
   ndef = 0;
   __syncwarp();
@@ -904,7 +911,8 @@ __device__ __forceinline__ void flush_deferred(const CheckArgs& a, const uint32_
   __syncwarp();
 }
 
-template <int FP, int FU, bool FUSE, int MINB>
+// SW = 1: sign bits (symbol width fixed at compile time); 0: read a.sw.
+template <int FP, int FU, bool FUSE, int MINB, int SW>
 __global__ void __launch_bounds__(kThreads, MINB)
 check_fields_kernel(CheckArgs a, const uint32_t* fields) {
   __shared__ __align__(16) WarpStage<FP> stg[kThreads / 32];
@@ -1216,7 +1224,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
           const uint32_t r = e >> 5, c = e & 31u;
           int h = 0;
 #pragma unroll
-          for (int w = 0; w < FU; ++w) h += __popc(sym_diff32(rowf0[r][w] ^ ws.cf0[c][w], a.sw));
+          for (int w = 0; w < FU; ++w) h += __popc(symd32<SW>(rowf0[r][w] ^ ws.cf0[c][w], a.sw));
           keep = h > a.d;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -1238,12 +1246,14 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
         uint32_t fr[FP];
 #pragma unroll
         for (int w = 0; w < FP; ++w) fr[w] = rowf[r][w];
-        if (gaps_differ<FP, FU>(fr, ws.cf[c], gapf) &&
-            fields_rest_ok<FP, FU>(fr, ws.cf[c], a.d, a.sw, hashed, keepf)) {
+        // a diagonal tile or packed runs dropped every pair equal on a gap
+        // block already (gap_peers): the gap test holds for all its pairs
+        if ((diag || gaps_differ<FP, FU>(fr, ws.cf[c], gapf)) &&
+            fields_rest_ok<FP, FU, SW>(fr, ws.cf[c], a.d, a.sw, hashed, keepf)) {
           ii = rowi[r];
           jj = ws.ci[c];
           if constexpr (FUSE) {  // replicates 1 .. q-1 in place
-            ok = !rep0 || replicates_ok_fields<FP>(a, fields, ii < jj ? ii : jj,
+            ok = !rep0 || replicates_ok_fields<FP, SW>(a, fields, ii < jj ? ii : jj,
                                                    ii < jj ? jj : ii, 1);
           } else {  // replicates 1 .. q-1 are tested later, 32 pairs at a time
             later = a.q > 1;
@@ -1253,7 +1263,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
       }
       const unsigned dbal = __ballot_sync(0xffffffffu, later);
       if (!FUSE && dbal) {
-        if (ndef + __popc(dbal) > 32u) flush_deferred<FP>(a, fields, ws, ndef, nout, lane);
+        if (ndef + __popc(dbal) > 32u) flush_deferred<FP, SW>(a, fields, ws, ndef, nout, lane);
         if (later) ws.def[ndef + __popc(dbal & ((1u << lane) - 1u))] = ordered_pair(ii, jj);
         ndef += __popc(dbal);
         __syncwarp();
@@ -1292,7 +1302,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
   }
   }
   if constexpr (!FUSE) {
-    flush_deferred<FP>(a, fields, ws, ndef, nout, lane);
+    flush_deferred<FP, SW>(a, fields, ws, ndef, nout, lane);
     flush_out<FP>(a, ws, nout, lane);
   } else {
     fuse_finish(a, acc, lane);
@@ -1468,14 +1478,19 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
     // the kernel loops over chunks of work until none is left: one wave of
     // as many CTAs as can be resident (or as tuned)
     void (*kern)(CheckArgs, const uint32_t*) = nullptr;
-#define MSM_CF(P, U, F, M) kern = check_fields_kernel<P, U, F, M>
-#define MSM_CHECK_FIELDS(P, U)                          \
-  if (!fuse && b.min_blocks == 6) MSM_CF(P, U, false, 6); \
-  else if (!fuse && b.min_blocks == 8) MSM_CF(P, U, false, 8); \
-  else if (!fuse) MSM_CF(P, U, false, 0);                \
-  else if (mb == 2) MSM_CF(P, U, true, 2);               \
-  else if (mb == 5) MSM_CF(P, U, true, 5);               \
-  else MSM_CF(P, U, true, 4)
+    // the default launches of sign-bit strings have the symbol width
+    // compiled in; tuned variants and E2LSH symbols read it at run time
+    const bool sign = a.sw == 1;
+#define MSM_CF(P, U, F, M, SW) kern = check_fields_kernel<P, U, F, M, SW>
+#define MSM_CHECK_FIELDS(P, U)                                  \
+  if (!fuse && b.min_blocks == 6) MSM_CF(P, U, false, 6, 0);     \
+  else if (!fuse && b.min_blocks == 8) MSM_CF(P, U, false, 8, 0); \
+  else if (!fuse && sign) MSM_CF(P, U, false, 0, 1);             \
+  else if (!fuse) MSM_CF(P, U, false, 0, 0);                     \
+  else if (mb == 2) MSM_CF(P, U, true, 2, 0);                    \
+  else if (mb == 5) MSM_CF(P, U, true, 5, 0);                    \
+  else if (sign) MSM_CF(P, U, true, 4, 1);                       \
+  else MSM_CF(P, U, true, 4, 0)
     switch (b.FU) {  // words holding fields: ceil(k / 2)
       case 1: MSM_CHECK_FIELDS(2, 1); break;
       case 2: MSM_CHECK_FIELDS(2, 2); break;
