@@ -245,6 +245,19 @@ __global__ void run_work_kernel(const uint32_t* starts, const uint32_t* ends,
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(checks, c);
 }
 
+// Segment (kept-block set) of batch position x < 2^32, x / n, without the
+// emulated 64-bit integer division: the float estimate carries a relative
+// error below 2^-21 and the quotient is a segment index below C(16, 8) <
+// 2^14, so the truncated estimate is within one of it, and one exact
+// comparison fixes it.
+__device__ __forceinline__ uint32_t seg_of(uint32_t x, int64_t n, float inv_n) {
+  uint32_t q = __float2uint_rz(__uint2float_rz(x) * inv_n);
+  const uint64_t p = (uint64_t)q * (uint64_t)n;
+  if (p > x) --q;
+  else if (p + (uint64_t)n <= x) ++q;
+  return q;
+}
+
 // ------------------------------------------------------------ pair check
 struct CheckArgs {
   const uint32_t* keys;     // sorted grouping keys (sub-group test)
@@ -259,6 +272,7 @@ struct CheckArgs {
   const uint32_t* ngroups;
   const uint64_t* strings;  // [Q][n][W]
   int64_t n;
+  float inv_n;  // 1 / n, for seg_of
   int W;
   int q;
   int d;
@@ -561,7 +575,7 @@ check_kernel(CheckArgs a) {
     const uint64_t local = item - a.work_prefix[g];
     const uint32_t st = a.starts[g];
     const uint32_t len = a.ends[g] - st + 1;
-    const int seg = (int)(st / a.n);
+    const int seg = (int)seg_of(st, a.n, a.inv_n);
     if (FUSE && g != cur_g) {
       cur_g = g;
       fuse_enter(a, acc, a.vals[st], lane);
@@ -826,6 +840,7 @@ __device__ __forceinline__ void load_fields(const uint32_t* pool, uint32_t idx,
 // when full, so the pairs of consecutive tiles lie together in E (the
 // recheck then finds their rows in L1).
 constexpr int kOut = 64;     // per-warp buffer of pairs for E
+constexpr int kCheckCtas = 4;  // resident pair-list check CTAs per SM
 constexpr int kQueue = 512;  // per-warp queue of pairs for the exact tests
 
 template <int FP>
@@ -974,7 +989,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
       // every member of the tile in one run of equal full keys: all its
       // pairs are equal on the first gap block, so none is reported here
       live = true;
-      if (a.masks[st / a.n].sub_width) {
+      if (a.masks[seg_of(st, a.n, a.inv_n)].sub_width) {
         const uint32_t last = min(len - 1, J * 32 + 31);
         live = a.keys[st + I * 32] != a.keys[st + last];
       }
@@ -988,7 +1003,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
     const uint32_t tlen = __shfl_sync(0xffffffffu, len, t);
     const uint32_t tI = __shfl_sync(0xffffffffu, I, t);
     const uint32_t tJ = __shfl_sync(0xffffffffu, J, t);
-    const int seg = (int)(tst / a.n);
+    const int seg = (int)seg_of(tst, a.n, a.inv_n);
     if (FUSE && tg != cur_g) {
       cur_g = tg;
       fuse_enter(a, acc, a.vals[tst], lane);
@@ -1019,7 +1034,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
         const int t2 = __ffs(lv) - 1;
         const uint32_t l2 = __shfl_sync(0xffffffffu, len, t2);
         const uint32_t s2 = __shfl_sync(0xffffffffu, st, t2);
-        if (l2 > (uint32_t)kSmall || ptotal + l2 > 32u || (int)(s2 / a.n) != seg) break;
+        if (l2 > (uint32_t)kSmall || ptotal + l2 > 32u || (int)seg_of(s2, a.n, a.inv_n) != seg) break;
         ptotal += l2;
         packmask |= 1u << t2;
         lv &= lv - 1;
@@ -1446,6 +1461,7 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   a.ngroups = g.ngroups;
   a.strings = b.strings;
   a.n = b.n;
+  a.inv_n = 1.0f / (float)b.n;
   a.W = b.W;
   a.q = b.q;
   a.d = b.d;
@@ -1508,6 +1524,22 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
     if (per_sm <= 0) {
       MSM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
       if (per_sm < 1) per_sm = 1;
+      // The pair list check gathers fields through L1: at most 4 CTAs per SM,
+      // with shared memory sized for them, so that the rest of the SM's
+      // 256 KB stays L1 (5 CTAs fit by registers, but left ~28 KB of L1 and
+      // ran 27 % slower).
+      if (!fuse && per_sm > kCheckCtas) {
+        per_sm = kCheckCtas;
+        cudaFuncAttributes fa;
+        int dev = 0, smem_sm = 0;
+        MSM_CUDA(cudaFuncGetAttributes(&fa, kern));
+        MSM_CUDA(cudaGetDevice(&dev));
+        MSM_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        const size_t need = (size_t)kCheckCtas * (fa.sharedSizeBytes + 1024);  // + per-CTA reserve
+        int pct = smem_sm > 0 ? (int)((need * 100 + smem_sm - 1) / smem_sm) : 100;
+        MSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      pct > 100 ? 100 : pct));
+      }
     }
     kern<<<num_sms() * per_sm, kThreads, 0, s>>>(a, b.fields);
     kt_end(s);
