@@ -25,6 +25,19 @@ constexpr int kSmall = 32;
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Segment (kept-block set) of batch position x < 2^32, x / n, without the
+// emulated 64-bit integer division: the float estimate carries a relative
+// error below 2^-21 and the quotient is a segment index below C(16, 8) <
+// 2^14, so the truncated estimate is within one of it, and one exact
+// comparison fixes it.
+__device__ __forceinline__ uint32_t seg_of(uint32_t x, int64_t n, float inv_n) {
+  uint32_t q = __float2uint_rz(__uint2float_rz(x) * inv_n);
+  const uint64_t p = (uint64_t)q * (uint64_t)n;
+  if (p > x) --q;
+  else if (p + (uint64_t)n <= x) ++q;
+  return q;
+}
+
 struct GroupWs {
   uint32_t* cnt_start;    // [chunks]
   uint32_t* cnt_end;      // [chunks]
@@ -108,6 +121,7 @@ constexpr int kStageWords = kChunk + 2 + (kChunk + 2) / 16 + 1;
 // with one neighbour on each side, are first staged in shared memory by
 // coalesced loads.
 __device__ __forceinline__ void chunk_flags(const uint32_t* keys, int64_t items, int64_t n,
+                                            float inv_n,
                                             const MaskDesc* masks, const uint32_t* sb,
                                             uint32_t* sk, uint32_t* fs_out,
                                             uint32_t* fe_out) {
@@ -120,8 +134,8 @@ __device__ __forceinline__ void chunk_flags(const uint32_t* keys, int64_t items,
   const int t0 = threadIdx.x * 16;
   const int64_t p0 = b0 + t0;
   uint32_t fs = 0, fe = 0;
-  int64_t local = p0 % n;
-  int64_t seg = p0 / n;
+  int64_t seg = seg_of((uint32_t)(p0 < items ? p0 : items - 1), n, inv_n);
+  int64_t local = p0 - seg * n;
   int sw = p0 < items ? masks[seg].sub_width : 0;
   uint32_t prev = sk[kslot(t0)] >> sw, cur = sk[kslot(t0 + 1)] >> sw;
   for (int j = 0; j < 16; ++j, ++local) {
@@ -152,13 +166,13 @@ __device__ __forceinline__ void chunk_flags(const uint32_t* keys, int64_t items,
   *fe_out = fe;
 }
 
-__global__ void run_count_kernel(const uint32_t* keys, int64_t items, int64_t n,
+__global__ void run_count_kernel(const uint32_t* keys, int64_t items, int64_t n, float inv_n,
                                  const MaskDesc* masks, const uint32_t* sb,
                                  uint32_t* cnt_start,
                                  uint32_t* cnt_end) {
   __shared__ uint32_t sk[kStageWords];
   uint32_t fs, fe;
-  chunk_flags(keys, items, n, masks, sb, sk, &fs, &fe);
+  chunk_flags(keys, items, n, inv_n, masks, sb, sk, &fs, &fe);
   uint32_t cs = __popc(fs), ce = __popc(fe);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -200,7 +214,7 @@ __device__ __forceinline__ uint32_t block_excl(uint32_t v, uint32_t* tmp,
   return x - v + pre;
 }
 
-__global__ void run_write_kernel(const uint32_t* keys, int64_t items, int64_t n,
+__global__ void run_write_kernel(const uint32_t* keys, int64_t items, int64_t n, float inv_n,
                                  const MaskDesc* masks, const uint32_t* sb,
                                  const uint32_t* off_start,
                                  const uint32_t* off_end, uint32_t* starts,
@@ -210,7 +224,7 @@ __global__ void run_write_kernel(const uint32_t* keys, int64_t items, int64_t n,
   __shared__ uint32_t sk[kStageWords];
   const int64_t p0 = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * 16;
   uint32_t fs, fe;  // bit j: start / end at p0 + j
-  chunk_flags(keys, items, n, masks, sb, sk, &fs, &fe);
+  chunk_flags(keys, items, n, inv_n, masks, sb, sk, &fs, &fe);
   uint32_t os = block_excl(__popc(fs), tmp, nullptr) + off_start[blockIdx.x];
   uint32_t oe = block_excl(__popc(fe), tmp, nullptr) + off_end[blockIdx.x];
   for (int j = 0; j < 16; ++j) {
@@ -243,19 +257,6 @@ __global__ void run_work_kernel(const uint32_t* starts, const uint32_t* ends,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(checks, c);
-}
-
-// Segment (kept-block set) of batch position x < 2^32, x / n, without the
-// emulated 64-bit integer division: the float estimate carries a relative
-// error below 2^-21 and the quotient is a segment index below C(16, 8) <
-// 2^14, so the truncated estimate is within one of it, and one exact
-// comparison fixes it.
-__device__ __forceinline__ uint32_t seg_of(uint32_t x, int64_t n, float inv_n) {
-  uint32_t q = __float2uint_rz(__uint2float_rz(x) * inv_n);
-  const uint64_t p = (uint64_t)q * (uint64_t)n;
-  if (p > x) --q;
-  else if (p + (uint64_t)n <= x) ++q;
-  return q;
 }
 
 // ------------------------------------------------------------ pair check
@@ -1413,7 +1414,8 @@ int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
   const int64_t chunks = (items + kChunk - 1) / kChunk;
   GroupWs g = carve(ws, items);
   kt_begin(KC_BOUNDS, s);
-  run_count_kernel<<<(unsigned)chunks, kThreads, 0, s>>>(b.keys, items, b.n, b.masks,
+  run_count_kernel<<<(unsigned)chunks, kThreads, 0, s>>>(b.keys, items, b.n,
+                                                        1.0f / (float)b.n, b.masks,
                                                         b.start_bits, g.cnt_start, g.cnt_end);
   kt_end(s);
   MSM_LAUNCH("run_count_kernel");
@@ -1423,8 +1425,8 @@ int find_groups(const PairBatch& b, void* ws, unsigned long long* checks_dev,
   if (rc) return rc;
   kt_begin(KC_BOUNDS, s);
   run_write_kernel<<<(unsigned)chunks, kThreads, 0, s>>>(
-      b.keys, items, b.n, b.masks, b.start_bits, g.off_start, g.off_end, g.starts, g.ends, chunks,
-      g.cnt_start, g.ngroups);
+      b.keys, items, b.n, 1.0f / (float)b.n, b.masks, b.start_bits, g.off_start, g.off_end,
+      g.starts, g.ends, chunks, g.cnt_start, g.ngroups);
   kt_end(s);
   MSM_LAUNCH("run_write_kernel");
   int grid = num_sms() * 4;
