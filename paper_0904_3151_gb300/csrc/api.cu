@@ -462,6 +462,13 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
   }
   int64_t count = 0, retries = 0;
 
+  // The candidate count is read once, after every replicate: a pair check
+  // that would pass the end of E stores nothing there but keeps counting,
+  // and then E grows to the final count and the whole enumeration runs
+  // again (its result does not depend on E).  No read-back between batches
+  // keeps the host off the GPU's path (and copies of earlier results on
+  // other streams from delaying it).
+  for (;;) {
   for (int q = 0; q < Q; ++q) {
     const uint64_t* pool = strings + (size_t)q * n * W;
     for (int m0 = 0; m0 < M; m0 += (int)Sb) {
@@ -513,42 +520,29 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
       tm.mark(3);
       rc = find_groups(pb, pws, checks_dev, s);
       if (rc) return rc;
-      if (fused) {  // candidates are rechecked and counted in place
-        tm.mark(4);
-        rc = check_groups(pb, pws, nullptr, 0, count_dev, s);
-        if (rc) return rc;
-        continue;
-      }
-      while (true) {
-        tm.mark(4);
-        rc = check_groups(pb, pws, cand, cap, count_dev, s);
-        if (rc) return rc;
-        tm.mark(-1);
-        unsigned long long c = 0;
-        rc = read_back(&c, count_dev, s);
-        if (rc) return rc;
-        if ((int64_t)c <= cap) {
-          count = (int64_t)c;
-          break;
-        }
-        // Candidate buffer too small: grow and redo this batch's checks.
-        int64_t ncap = (int64_t)c + (int64_t)c / 2 + 1024;
-        if (ncap < 2 * cap) ncap = 2 * cap;
-        uint64_t* nb = (uint64_t*)sc.get(8 * (size_t)ncap);
-        if (!nb) return MSM_E_NOMEM;
-        if (count > 0)
-          MSM_CUDA(cudaMemcpyAsync(nb, cand, 8 * (size_t)count, cudaMemcpyDeviceToDevice, s));
-        sc.put(cand);
-        cand = nb;
-        cap = ncap;
-        unsigned long long reset = (unsigned long long)count;
-        MSM_CUDA(cudaMemcpyAsync(count_dev, &reset, sizeof(reset), cudaMemcpyHostToDevice, s));
-        MSM_CUDA(cudaStreamSynchronize(s));
-        ++retries;
-      }
+      tm.mark(4);
+      rc = check_groups(pb, pws, fused ? nullptr : cand, fused ? 0 : cap, count_dev, s);
+      if (rc) return rc;
     }
   }
   tm.mark(-1);
+  if (fused) break;  // candidates were rechecked and counted in place
+  unsigned long long c = 0;
+  int rc = read_back(&c, count_dev, s);
+  if (rc) return rc;
+  if ((int64_t)c <= cap) {
+    count = (int64_t)c;
+    break;
+  }
+  // E was too small: grow it to the final count and enumerate again.
+  int64_t ncap = (int64_t)c + (int64_t)c / 8 + 1024;
+  sc.put(cand);
+  cand = (uint64_t*)sc.get(8 * (size_t)ncap);
+  if (!cand) return MSM_E_NOMEM;
+  cap = ncap;
+  MSM_CUDA(cudaMemsetAsync(counters, 0, 256, s));
+  ++retries;
+  }
   total_cand = count;
   if (fused && st) {
     unsigned long long c = 0;
