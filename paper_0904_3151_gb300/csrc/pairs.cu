@@ -844,13 +844,17 @@ constexpr int kOut = 64;     // per-warp buffer of pairs for E
 constexpr int kCheckCtas = 4;  // resident pair-list check CTAs per SM
 constexpr int kQueue = 512;  // per-warp queue of pairs for the exact tests
 
-template <int FP>
+// Field words are staged with an odd row stride SF (FU rounded up to odd):
+// 32 lanes reading the words of 32 different columns then hit 32 different
+// banks (the even stride of the padded global layout made two columns share
+// a bank).
+template <int FP, int SF>
 struct WarpStage {
-  uint32_t cf[32][FP];   // column block: fields of this replicate
-  uint32_t cf0[32][FP];  // and of replicate 0
+  uint32_t cf[32][SF];   // column block: fields of this replicate
+  uint32_t cf0[32][SF];  // and of replicate 0
   uint32_t ci[32];       // points
-  uint32_t rf[32][FP];   // rows of the current tile (off-diagonal)
-  uint32_t rf0[32][FP];
+  uint32_t rf[32][SF];   // rows of the current tile (off-diagonal)
+  uint32_t rf0[32][SF];
   uint32_t ri[32];
   uint32_t ref[kMaxFieldBlocks];    // reference value per gap block
   uint32_t colat[kMaxFieldBlocks];  // columns at the reference
@@ -859,9 +863,8 @@ struct WarpStage {
 };
 
 // Appends the warp's buffered pairs to E (one atomic).
-template <int FP>
-__device__ __forceinline__ void flush_out(const CheckArgs& a, WarpStage<FP>& ws, uint32_t& nout,
-                                          int lane) {
+template <class WS>
+__device__ __forceinline__ void flush_out(const CheckArgs& a, WS& ws, uint32_t& nout, int lane) {
   if (!nout) return;
   __syncwarp();
   unsigned long long b = 0;
@@ -905,9 +908,9 @@ __device__ __forceinline__ uint32_t gap_peers(const uint32_t (&f)[FP], uint32_t 
 // round trip; collected 32 at a time, a warp waits once per 32 such pairs.
 // Passing pairs join the E buffer.  (The count-only form tests them in
 // place: its distance evaluation follows each batch.)
-template <int FP, int SW>
+template <int FP, int SW, class WS>
 __device__ __forceinline__ void flush_deferred(const CheckArgs& a, const uint32_t* fields,
-                                               WarpStage<FP>& ws, uint32_t& ndef,
+                                               WS& ws, uint32_t& ndef,
                                                uint32_t& nout, int lane) {
   if (!ndef) return;
   __syncwarp();
@@ -921,7 +924,7 @@ __device__ __forceinline__ void flush_deferred(const CheckArgs& a, const uint32_
   __syncwarp();
   const unsigned bal = __ballot_sync(0xffffffffu, ok);
   if (!bal) return;
-  if (nout + __popc(bal) > (uint32_t)kOut) flush_out<FP>(a, ws, nout, lane);
+  if (nout + __popc(bal) > (uint32_t)kOut) flush_out(a, ws, nout, lane);
   if (ok) ws.out[nout + __popc(bal & ((1u << lane) - 1u))] = pr;
   nout += __popc(bal);
   __syncwarp();
@@ -931,11 +934,12 @@ __device__ __forceinline__ void flush_deferred(const CheckArgs& a, const uint32_
 template <int FP, int FU, bool FUSE, int MINB, int SW>
 __global__ void __launch_bounds__(kThreads, MINB)
 check_fields_kernel(CheckArgs a, const uint32_t* fields) {
-  __shared__ __align__(16) WarpStage<FP> stg[kThreads / 32];
+  constexpr int SF = FU | 1;
+  __shared__ __align__(16) WarpStage<FP, SF> stg[kThreads / 32];
   __shared__ uint64_t sm_q[FUSE ? kThreads / 32 : 1][32];  // fused recheck queue
   __shared__ uint16_t sm_qs[kThreads / 32][kQueue];       // queued pairs: row << 5 | column
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  WarpStage<FP>& ws = stg[warp];
+  WarpStage<FP, SF>& ws = stg[warp];
   const uint64_t total = *a.total_work;
   const uint32_t G = *a.ngroups;
   if (total == 0 || G == 0) return;
@@ -1077,7 +1081,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
         if (rep0) load_fields<FP>(pool0, ic, f0);
       }
 #pragma unroll
-      for (int w = 0; w < FP; ++w) {
+      for (int w = 0; w < FU; ++w) {
         ws.cf[lane][w] = f[w];
         ws.cf0[lane][w] = f0[w];
       }
@@ -1105,7 +1109,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
         if (rep0) load_fields<FP>(pool0, ic, f0);
       }
 #pragma unroll
-      for (int w = 0; w < FP; ++w) {
+      for (int w = 0; w < FU; ++w) {
         ws.cf[lane][w] = f[w];
         ws.cf0[lane][w] = f0[w];
       }
@@ -1142,7 +1146,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
     uint32_t fa[FP];
     if (diag) {
 #pragma unroll
-      for (int w = 0; w < FP; ++w) fa[w] = ws.cf[lane][w];
+      for (int w = 0; w < FP; ++w) fa[w] = w < FU ? ws.cf[lane][w] : 0u;
     } else {
       uint32_t f0[FP];
       uint32_t ia = 0;
@@ -1154,7 +1158,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
         if (rep0) load_fields<FP>(pool0, ia, f0);
       }
 #pragma unroll
-      for (int w = 0; w < FP; ++w) {
+      for (int w = 0; w < FU; ++w) {
         ws.rf[lane][w] = fa[w];
         ws.rf0[lane][w] = f0[w];
       }
@@ -1219,8 +1223,8 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
     }
     __syncwarp();
     evaluated += nq;
-    const uint32_t (*rowf)[FP] = diag ? ws.cf : ws.rf;
-    const uint32_t (*rowf0)[FP] = diag ? ws.cf0 : ws.rf0;
+    const uint32_t (*rowf)[SF] = diag ? ws.cf : ws.rf;
+    const uint32_t (*rowf0)[SF] = diag ? ws.cf0 : ws.rf0;
     const uint32_t* rowi = diag ? ws.ci : ws.ri;
     // In a later replicate most queued pairs were already within d in
     // replicate 0 (Appendix, first trick) and are rejected there: that test
@@ -1261,7 +1265,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
         const uint32_t r = e >> 5, c = e & 31u;
         uint32_t fr[FP];
 #pragma unroll
-        for (int w = 0; w < FP; ++w) fr[w] = rowf[r][w];
+        for (int w = 0; w < FP; ++w) fr[w] = w < FU ? rowf[r][w] : 0u;
         // a diagonal tile or packed runs dropped every pair equal on a gap
         // block already (gap_peers): the gap test holds for all its pairs
         if ((diag || gaps_differ<FP, FU>(fr, ws.cf[c], gapf)) &&
@@ -1295,7 +1299,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
     }
     if (!FUSE && npass) {
       __syncwarp();
-      if (nout + npass > (uint32_t)kOut) flush_out<FP>(a, ws, nout, lane);
+      if (nout + npass > (uint32_t)kOut) flush_out(a, ws, nout, lane);
       if (npass > (uint32_t)kOut) {  // a tile with many pairs: its own append
         unsigned long long b1 = 0;
         if (lane == 0) b1 = atomicAdd(a.count, (unsigned long long)npass);
@@ -1319,7 +1323,7 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
   }
   if constexpr (!FUSE) {
     flush_deferred<FP, SW>(a, fields, ws, ndef, nout, lane);
-    flush_out<FP>(a, ws, nout, lane);
+    flush_out(a, ws, nout, lane);
   } else {
     fuse_finish(a, acc, lane);
   }
