@@ -342,6 +342,14 @@ static int check_sets(const int64_t* off, int S, int64_t* n) {
 }
 
 // Count-only recheck fused into the pair check (X == NULL: not fused).
+// Dense-tile records of a pair-list run (run_msm with recs_out): the
+// records themselves and how many there are, and the pairs they hold.
+struct RecsOut {
+  TileRecs recs;
+  uint32_t nrec = 0;
+  int64_t pairs = 0;
+};
+
 struct FuseCfg {
   const void* X = nullptr;
   int dtype = 0, dim = 0, metric = 0;
@@ -377,7 +385,8 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
                    uint64_t** cand_out, int64_t* count_out, msm_stats* st,
                    PhaseTimer& tm, const SetTable& sets = SetTable(),
                    const FuseCfg& fz = FuseCfg(),
-                   unsigned long long** counters_out = nullptr) {
+                   unsigned long long** counters_out = nullptr,
+                   RecsOut* recs_out = nullptr) {
   cudaStream_t s = sc.stream();
   const bool fused = fz.X != nullptr;
   int64_t total_cand = 0;
@@ -460,6 +469,19 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
     cand = (uint64_t*)sc.get(8 * (size_t)cap);
     if (!cand) return MSM_E_NOMEM;
   }
+  // Dense tiles as records (pair-list ε graph): a pool of as many bytes as E,
+  // and room for one record per 16 slots of E; a full pool only sends tiles
+  // back to E.
+  TileRecs recs;
+  if (!fused && recs_out) {
+    recs.pool_cap = (uint64_t)2 * (uint64_t)cap;
+    if (recs.pool_cap > 0xFFFFFFF0ull) recs.pool_cap = 0xFFFFFFF0ull;  // 32-bit offsets
+    recs.cap = (uint32_t)(cap / 16 + 1024);
+    recs.pool = (uint32_t*)sc.get(4 * (size_t)recs.pool_cap);
+    recs.offs = (uint32_t*)sc.get(4 * (size_t)recs.cap);
+    if (!recs.pool || !recs.offs) return MSM_E_NOMEM;
+    recs.ctr = counters + 4;  // cleared with the other counters
+  }
   int64_t count = 0, retries = 0;
 
   // The candidate count is read once, after every replicate: a pair check
@@ -517,6 +539,7 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
       pb.evaluated = eval_dev;
       pb.ctas_per_sm = tu.check_ctas_per_sm;
       pb.min_blocks = tu.check_min_blocks;
+      pb.recs = recs;
       tm.mark(3);
       rc = find_groups(pb, pws, checks_dev, s);
       if (rc) return rc;
@@ -544,6 +567,15 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
   ++retries;
   }
   total_cand = count;
+  if (recs.pool) {
+    unsigned long long h[3] = {0, 0, 0};
+    MSM_CUDA(cudaMemcpyAsync(h, recs.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    MSM_CUDA(cudaStreamSynchronize(s));
+    recs_out->recs = recs;
+    recs_out->nrec = (uint32_t)(h[0] < recs.cap ? h[0] : recs.cap);
+    recs_out->pairs = (int64_t)h[2];
+    total_cand += (int64_t)h[2];
+  }
   if (fused && st) {
     unsigned long long c = 0;
     int rc = read_back(&c, count_dev, s);
@@ -1137,9 +1169,13 @@ static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, i
     fz.kept = ctr;
     fz.set_kept = set_kept;
   }
+  // pair-list output: dense tiles become records that the recheck reads with
+  // their rows staged once (rows of up to 1 KB)
+  RecsOut ro;
+  const bool use_recs = mode != MSM_OUT_COUNT && !pc && tile_recheck_supported(Xd, dtype, dim);
   rc = run_msm(sc, strings, n, ell, sw, k, d, Q, tuning_of(params),
                params->cand_capacity, &cand, &m, stats, tm, sets, fz,
-               pc ? &pc->counters : nullptr);
+               pc ? &pc->counters : nullptr, use_recs ? &ro : nullptr);
   if (rc) return rc;
   if (pc) {  // results stay on the device for the plan
     pc->ctr = ctr;
@@ -1152,11 +1188,12 @@ static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, i
   // A8: recheck into the output buffers.
   uint64_t* pairs = nullptr;
   float* dist = nullptr;
-  if (mode != MSM_OUT_COUNT && m > 0) {
-    pairs = (uint64_t*)sc.get(8 * (size_t)m);
+  const int64_t m_all = m + ro.pairs;  // candidates in E and in records
+  if (mode != MSM_OUT_COUNT && m_all > 0) {
+    pairs = (uint64_t*)sc.get(8 * (size_t)m_all);
     if (!pairs) return MSM_E_NOMEM;
     if (mode == MSM_OUT_PAIRS_DIST) {
-      dist = (float*)sc.get(4 * (size_t)m);
+      dist = (float*)sc.get(4 * (size_t)m_all);
       if (!dist) return MSM_E_NOMEM;
     }
   }
@@ -1164,11 +1201,18 @@ static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, i
   rc = launch_recheck(Xd, dtype, n, dim, metric, eps, n32, cand, nullptr, m,
                       pairs, dist, ctr, ctr + 1, nullptr, s);
   if (rc) return rc;
+  rc = launch_recheck_tiles(Xd, dtype, n, dim, metric, eps, n32, ro.recs, ro.nrec, pairs, dist,
+                            ctr, ctr + 1, s);
+  if (rc) return rc;
   unsigned long long h[3] = {0, 0, 0};
   MSM_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
   MSM_CUDA(cudaStreamSynchronize(s));
   const int64_t kept = (int64_t)h[0];
   sc.put(cand);
+  if (ro.recs.pool) {
+    sc.put(ro.recs.pool);
+    sc.put(ro.recs.offs);
+  }
   if ((params->flags & MSM_FLAG_CANONICAL) && pairs && kept > 1) {
     tm.mark(6);
     void* ws = sc.get(sort64_scratch_bytes(kept));

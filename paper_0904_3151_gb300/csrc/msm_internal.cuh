@@ -223,6 +223,26 @@ int sort_pairs64(uint64_t* keys, uint32_t* vals, int64_t m, int key_bits,
                  void* ws, cudaStream_t s);
 
 // pairs.cu: group boundaries and the in-group pair check.
+// Dense tiles of the pair-list check.  A tile whose passing pairs are many
+// is stored as one record instead of one candidate per pair, so that the
+// recheck reads the tile's rows once (recheck_tiles in recheck.cu).  Record
+// at word offset o of pool: [o] = number of entries | (rows are the columns)
+// << 31; [o + 1, o + 33) the row points; [o + 33, o + 65) the column points;
+// then the entries (row << 5 | column), two 16-bit entries per word.  offs[r]
+// is record r's offset, or kNoRecord when the pool was full (its pairs went to
+// the candidate list instead).  ctr: [0] records reserved, [1] pool words
+// reserved, [2] pairs stored in records.
+constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
+constexpr int kRecHeader = 65;
+struct TileRecs {
+  uint32_t* pool = nullptr;  // NULL: no records, every candidate goes to E
+  uint64_t pool_cap = 0;     // words
+  uint32_t* offs = nullptr;
+  uint32_t cap = 0;          // records
+  unsigned long long* ctr = nullptr;
+  uint32_t min_pairs = 32;   // a tile with fewer passing pairs appends them to E
+};
+
 struct PairBatch {
   const uint32_t* keys;      // sorted keys [S*n]
   const uint32_t* vals;      // point index of each sorted item [S*n]
@@ -255,6 +275,7 @@ struct PairBatch {
   int sw = 1;                            // bits per symbol (1: sign bits)
   unsigned long long* evaluated = nullptr;  // pairs that took the per-pair
                                            // tests after the prefilter
+  TileRecs recs;                         // dense-tile records (pair-list eps graph)
   // launch tuning of the pair check (0 = defaults)
   int ctas_per_sm = 0;
   int min_blocks = 0;                    // fused variant: 2, 4 or 5
@@ -301,6 +322,14 @@ int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
                    unsigned long long* count_dev,
                    unsigned long long* recompute_dev, unsigned* bad_dev,
                    cudaStream_t s);
+// The recheck of the dense-tile records 0 .. nrec - 1 (offsets in recs.offs),
+// appending kept pairs and distances after those already in the output.
+int launch_recheck_tiles(const void* X, int dtype, int64_t n, int dim, int metric, float eps,
+                         const float* nrm32, const TileRecs& recs, uint32_t nrec,
+                         uint64_t* pairs_out, float* dist_out, unsigned long long* count_dev,
+                         unsigned long long* recompute_dev, cudaStream_t s);
+// Whether rows of this shape can be staged whole by recheck_tiles.
+bool tile_recheck_supported(const void* X, int dtype, int dim);
 int launch_eps_count(const void* X, int dtype, int64_t n, int dim, int metric,
                      float eps, const float* nrm32,
                      unsigned long long* count_dev, cudaStream_t s);

@@ -294,6 +294,7 @@ struct CheckArgs {
   int nsets;
   int sw;  // bits per symbol: Hamming distances count differing symbols
   unsigned long long* evaluated;  // pairs that took the per-pair tests (or NULL)
+  TileRecs recs;                  // dense-tile records (pool NULL: none)
 };
 
 // Number of differing symbols in x = a ^ b (symbols of sw = 1, 2 or 4 bits
@@ -1297,7 +1298,42 @@ check_fields_kernel(CheckArgs a, const uint32_t* fields) {
         npass += __popc(bal);
       }
     }
-    if (!FUSE && npass) {
+    // A tile (or packed pass) with many passing pairs becomes one record of
+    // its points and entries, which the recheck reads with the tile's rows
+    // staged once; if the record pool is full its pairs join E as usual.
+    bool recorded = false;
+    if (!FUSE && a.recs.pool && npass >= a.recs.min_pairs) {
+      __syncwarp();
+      const uint32_t words = (uint32_t)kRecHeader + (npass + 1) / 2;
+      unsigned long long o = ~0ull, idx = 0;
+      if (lane == 0) {
+        idx = atomicAdd(a.recs.ctr, 1ull);
+        if (idx < (unsigned long long)a.recs.cap) {
+          o = atomicAdd(a.recs.ctr + 1, (unsigned long long)words);
+          if (o + words <= a.recs.pool_cap) atomicAdd(a.recs.ctr + 2, (unsigned long long)npass);
+          else o = ~0ull;
+        }
+      }
+      idx = __shfl_sync(0xffffffffu, idx, 0);
+      o = __shfl_sync(0xffffffffu, o, 0);
+      if (o != ~0ull) {
+        uint32_t* R = a.recs.pool + o;
+        if (lane == 0) R[0] = npass | (diag ? 0x80000000u : 0u);
+        R[1 + lane] = rowi[lane];
+        R[33 + lane] = ws.ci[lane];
+        for (uint32_t t2 = lane; 2 * t2 < npass; t2 += 32) {
+          const uint32_t lo = sm_qs[warp][2 * t2];
+          const uint32_t hi = 2 * t2 + 1 < npass ? (uint32_t)sm_qs[warp][2 * t2 + 1] : 0u;
+          R[kRecHeader + t2] = lo | (hi << 16);
+        }
+        if (lane == 0) a.recs.offs[idx] = (uint32_t)o;
+        recorded = true;
+      } else if (lane == 0 && idx < (unsigned long long)a.recs.cap) {
+        a.recs.offs[idx] = kNoRecord;
+      }
+      __syncwarp();
+    }
+    if (!FUSE && npass && !recorded) {
       __syncwarp();
       if (nout + npass > (uint32_t)kOut) flush_out(a, ws, nout, lane);
       if (npass > (uint32_t)kOut) {  // a tile with many pairs: its own append
@@ -1490,6 +1526,7 @@ int check_groups(const PairBatch& b, void* ws, uint64_t* cand, int64_t cap,
   a.nsets = b.nsets;
   a.sw = b.sw > 0 ? b.sw : 1;
   a.evaluated = b.evaluated;
+  a.recs = b.recs;
   const bool fuse = b.X != nullptr;
   if (fuse && !b.kept) return set_error("fused recheck needs counters"), MSM_E_INVAL;
   const int mb = b.min_blocks ? b.min_blocks : 4;

@@ -155,7 +155,191 @@ eps_count_kernel(const void* X, int dtype, int64_t n, int dim, int metric,
   if ((tid & 31) == 0 && c) atomicAdd(count, c);
 }
 
+// ------------------------------------------------------ dense-tile records
+// One CTA of 4 warps per record: the record's 32 or 64 rows are copied whole
+// into shared memory (16-byte cp.async, through L2 only), then every listed
+// pair takes the decision of recheck_kernel with its sum taken from shared
+// memory, one pair per lane.  The rows of a tile are thus read once for all
+// its pairs instead of once per pair through L1.
+constexpr int kTileThreads = 128;
+constexpr int kTileStage = 64;          // kept pairs staged per warp before one append
+constexpr int kTileRowBytesMax = 1024;  // rows staged whole up to 1 KB
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// S = sum (a_c - b_c)^2 of two rows held in shared memory as nch 16-byte
+// chunks (nch even).  A lane starts at chunk `rot` mod nch and wraps around,
+// so the 8 lanes of a quarter warp read 8 different chunks (32 different
+// banks) whatever rows they hold.  Eight fma chains over at most dim / 8
+// coordinates each: with the difference's rounding (2u in its square) and
+// three levels combining the chains, |S' - S| <= (dim / 8 + 8) u S.
+__device__ __forceinline__ float smem_sq_dist(const unsigned char* a, const unsigned char* b,
+                                              int nch, int dtype, int rot) {
+  const uint4* a4 = reinterpret_cast<const uint4*>(a);
+  const uint4* b4 = reinterpret_cast<const uint4*>(b);
+  float c[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) c[m] = 0.f;
+  int q = rot % nch;
+  for (int t = 0; t < nch; t += 2) {
+    const int q1 = q + 1 == nch ? 0 : q + 1;
+    const uint4 x0 = a4[q], y0 = b4[q], x1 = a4[q1], y1 = b4[q1];
+    if (dtype == MSM_DT_BF16) {  // 8 values per chunk: value v of a chunk feeds chain v
+      const uint32_t xa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      const uint32_t ya[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const float t0 = __uint_as_float(xa[w] << 16) - __uint_as_float(ya[w] << 16);
+        const float t1 = __uint_as_float(xa[w] & 0xffff0000u) - __uint_as_float(ya[w] & 0xffff0000u);
+        c[(2 * w) & 7] = fmaf(t0, t0, c[(2 * w) & 7]);
+        c[(2 * w + 1) & 7] = fmaf(t1, t1, c[(2 * w + 1) & 7]);
+      }
+    } else {  // 4 floats per chunk: the first chunk feeds chains 0-3, the second 4-7
+      const float d0 = __uint_as_float(x0.x) - __uint_as_float(y0.x);
+      const float d1 = __uint_as_float(x0.y) - __uint_as_float(y0.y);
+      const float d2 = __uint_as_float(x0.z) - __uint_as_float(y0.z);
+      const float d3 = __uint_as_float(x0.w) - __uint_as_float(y0.w);
+      const float d4 = __uint_as_float(x1.x) - __uint_as_float(y1.x);
+      const float d5 = __uint_as_float(x1.y) - __uint_as_float(y1.y);
+      const float d6 = __uint_as_float(x1.z) - __uint_as_float(y1.z);
+      const float d7 = __uint_as_float(x1.w) - __uint_as_float(y1.w);
+      c[0] = fmaf(d0, d0, c[0]);
+      c[1] = fmaf(d1, d1, c[1]);
+      c[2] = fmaf(d2, d2, c[2]);
+      c[3] = fmaf(d3, d3, c[3]);
+      c[4] = fmaf(d4, d4, c[4]);
+      c[5] = fmaf(d5, d5, c[5]);
+      c[6] = fmaf(d6, d6, c[6]);
+      c[7] = fmaf(d7, d7, c[7]);
+    }
+    q = q1 + 1 == nch ? 0 : q1 + 1;
+  }
+  return ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+}
+
+__global__ void __launch_bounds__(kTileThreads)
+recheck_tiles_kernel(const void* X, int dtype, int64_t n, int dim, int metric, float eps,
+                     const float* nrm, const uint32_t* pool, const uint32_t* offs, uint32_t nrec,
+                     uint64_t* pairs_out, float* dist_out, unsigned long long* count,
+                     unsigned long long* recompute, float relS) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  const int rowb = dim * (dtype == MSM_DT_BF16 ? 2 : 4), nch = rowb / 16;
+  unsigned char* rows = tsm;                                            // [64][rowb]
+  uint32_t* pts = reinterpret_cast<uint32_t*>(tsm + 64 * (size_t)rowb);  // [64]
+  uint64_t* st_p = reinterpret_cast<uint64_t*>(pts + 64);               // [4][kTileStage]
+  float* st_d = reinterpret_cast<float*>(st_p + 4 * kTileStage);         // [4][kTileStage]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint64_t* wp = st_p + warp * kTileStage;
+  float* wd = st_d + warp * kTileStage;
+  uint32_t ns = 0;
+  unsigned long long nre = 0;
+  auto flush = [&]() {
+    __syncwarp();
+    unsigned long long b0 = 0;
+    if (lane == 0) b0 = atomicAdd(count, (unsigned long long)ns);
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    for (uint32_t t = lane; t < ns; t += 32) {
+      if (pairs_out)
+        __stcs(reinterpret_cast<unsigned long long*>(pairs_out) + b0 + t,
+               (unsigned long long)wp[t]);
+      if (dist_out) __stcs(dist_out + b0 + t, wd[t]);
+    }
+    __syncwarp();
+    ns = 0;
+  };
+  for (uint32_t rec = blockIdx.x; rec < nrec; rec += gridDim.x) {
+    const uint32_t o = __ldg(offs + rec);
+    if (o == kNoRecord) continue;  // the same for every thread
+    const uint32_t* R = pool + o;
+    const uint32_t hd = __ldg(R);
+    const uint32_t ne = hd & 0x7FFFFFFFu;
+    const bool same = (hd >> 31) != 0u;
+    const int nr = same ? 32 : 64;
+    __syncthreads();  // the previous record's pairs are done with the rows
+    if (tid < 64) pts[tid] = __ldg(R + 1 + tid);
+    __syncthreads();
+    for (int t = tid; t < nr * nch; t += kTileThreads) {
+      const int sl = t / nch, ch = t - sl * nch;
+      cp_async16(rows + (size_t)sl * rowb + ch * 16,
+                 reinterpret_cast<const unsigned char*>(X) + (size_t)pts[sl] * rowb + ch * 16);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (uint32_t e0 = (uint32_t)warp * 32; e0 < ne; e0 += kTileThreads) {
+      const uint32_t e = e0 + lane;
+      bool keep = false;
+      double delta = 0.0;
+      uint64_t pr = 0;
+      if (e < ne) {
+        const uint32_t ent = (__ldg(R + kRecHeader + (e >> 1)) >> (16 * (e & 1u))) & 0xFFFFu;
+        const int r = (int)(ent >> 5), cs = same ? (int)(ent & 31u) : 32 + (int)(ent & 31u);
+        const float S = smem_sq_dist(rows + (size_t)r * rowb, rows + (size_t)cs * rowb, nch,
+                                     dtype, lane);
+        const uint32_t i = pts[r], j = pts[cs];
+        const float ni = metric == MSM_COSINE ? nrm[i] : 0.f;
+        const float nj = metric == MSM_COSINE ? nrm[j] : 0.f;
+        bool exact = false;
+        delta = decide(X, dtype, i, j, dim, metric, eps, S, ni, nj, relS, true, &keep, &exact);
+        nre += exact;
+        pr = i < j ? (((uint64_t)i << 32) | j) : (((uint64_t)j << 32) | i);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const uint32_t pos = ns + __popc(bal & ((1u << lane) - 1u));
+        wp[pos] = pr;
+        wd[pos] = (float)delta;
+      }
+      ns += __popc(bal);
+      if (ns > (uint32_t)(kTileStage - 32)) flush();
+    }
+  }
+  if (ns) flush();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, o);
+  if (lane == 0 && nre) atomicAdd(recompute, nre);
+}
+
 }  // namespace
+
+bool tile_recheck_supported(const void* X, int dtype, int dim) {
+  const int rowb = dim * (dtype == MSM_DT_BF16 ? 2 : 4);
+  // whole pairs of 16-byte chunks (smem_sq_dist takes two per step)
+  return rowb % 32 == 0 && rowb <= kTileRowBytesMax && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+}
+
+int launch_recheck_tiles(const void* X, int dtype, int64_t n, int dim, int metric, float eps,
+                         const float* nrm32, const TileRecs& recs, uint32_t nrec,
+                         uint64_t* pairs_out, float* dist_out, unsigned long long* count_dev,
+                         unsigned long long* recompute_dev, cudaStream_t s) {
+  if (nrec == 0) return MSM_OK;
+  if (!tile_recheck_supported(X, dtype, dim))
+    return set_error("dense-tile recheck: unsupported row shape"), MSM_E_INVAL;
+  const int rowb = dim * (dtype == MSM_DT_BF16 ? 2 : 4);
+  const size_t smem = 64 * (size_t)rowb + 64 * 4 + 4 * kTileStage * (8 + 4);
+  MSM_CUDA(cudaFuncSetAttribute(recheck_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  int per_sm = 0;
+  MSM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, recheck_tiles_kernel,
+                                                         kTileThreads, smem));
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms() * per_sm;
+  if (grid > (int64_t)nrec) grid = nrec;
+  // eight chains of at most dim / 8 terms (smem_sq_dist)
+  const float relS = (float)(dim / 8 + 8) * (float)kU;
+  kt_begin(KC_RECHECK, s);
+  recheck_tiles_kernel<<<(int)grid, kTileThreads, smem, s>>>(
+      X, dtype, n, dim, metric, eps, nrm32, recs.pool, recs.offs, nrec, pairs_out, dist_out,
+      count_dev, recompute_dev, relS);
+  kt_end(s);
+  MSM_LAUNCH("recheck_tiles_kernel");
+  return MSM_OK;
+}
 
 int launch_recheck(const void* X, int dtype, int64_t n, int dim, int metric,
                    float eps, const float* nrm, const uint64_t* cand,
