@@ -939,15 +939,17 @@ def main():
                                         "frac": per_rep / (t / 1000.0) / 1e9 / peaks["hbm_gbs"],
                                         "ms_per_replicate": t}
     if klaunch.get("recheck"):
-        # the recheck gathers two rows per candidate, mostly from L2 (X is
-        # read ~1 KB per candidate but only 512 MB from DRAM): a gather rate,
-        # not an HBM fraction
+        # the recheck reads two rows per candidate: the candidates of dense
+        # tiles from their tile's rows staged once in shared memory, the rest
+        # gathered through L1 and L2 -- a rate of rows consumed, not an HBM
+        # fraction (X is 512 MB; the rows come mostly from L2)
         row_bytes, _, _ = algorithmic("recheck", st, n, wl.dim, Q, W_words)
-        avg_ms = kms["recheck"] / klaunch["recheck"]
+        ms_step = kms["recheck"] / a.steps
         hbm_kernels["recheck_gather"] = {
-            "row_bytes_per_s_GB": row_bytes / (avg_ms / 1000.0) / 1e9, "avg_launch_ms": avg_ms,
+            "row_bytes_per_s_GB": row_bytes / (ms_step / 1000.0) / 1e9, "ms_per_step": ms_step,
             "launches_per_step": klaunch["recheck"] // a.steps,
-            "note": "candidate rows gathered from L2 (mostly) and DRAM; latency-bound"}
+            "note": "rows of 2 points per candidate consumed per second (dense tiles staged "
+                    "once per tile, other candidates gathered); latency-bound"}
     if dom in hbm_kernels:
         h = hbm_kernels[dom]
         roof = {"kernel": dom, "bound": "hbm", "achieved": h["achieved"], "peak": peaks["hbm_gbs"],

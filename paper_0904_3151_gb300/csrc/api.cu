@@ -469,9 +469,10 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
     cand = (uint64_t*)sc.get(8 * (size_t)cap);
     if (!cand) return MSM_E_NOMEM;
   }
-  // Dense tiles as records (pair-list ε graph): a pool of as many bytes as E,
-  // and room for one record per 16 slots of E; a full pool only sends tiles
-  // back to E.
+  // Dense tiles as records (pair-list ε graph; at least 64 passing pairs: 32
+  // and 96 were ~1 ms slower per step at the scale workload): a pool of as
+  // many bytes as E, and room for one record per 16 slots of E; a full pool
+  // only sends tiles back to E.
   TileRecs recs;
   if (!fused && recs_out) {
     recs.pool_cap = (uint64_t)2 * (uint64_t)cap;

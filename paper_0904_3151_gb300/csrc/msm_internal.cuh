@@ -240,7 +240,7 @@ struct TileRecs {
   uint32_t* offs = nullptr;
   uint32_t cap = 0;          // records
   unsigned long long* ctr = nullptr;
-  uint32_t min_pairs = 32;   // a tile with fewer passing pairs appends them to E
+  uint32_t min_pairs = 64;   // a tile with fewer passing pairs appends them to E
 };
 
 struct PairBatch {
