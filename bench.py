@@ -82,8 +82,11 @@ def train_projection(msm, Xt, eps, ell, k, d, seed, n_pairs=1 << 21, steps=1000)
     import torch
     t0 = time.perf_counter()
     n = Xt.shape[0]
+    # canonical order: the output order follows the GPU's atomics, and the
+    # positives are drawn from the list by index, so this keeps the training
+    # set (and the network) the same from run to run
     pos, _, _ = msm.eps_graph(Xt, msm.COSINE, eps, ell, k, d, Q=4, seed=seed,
-                              out_mode=1, cand_capacity=800 * n)
+                              out_mode=1, cand_capacity=800 * n, canonical=True)
     g = torch.Generator(device="cuda").manual_seed(7)
     npos = min(pos.numel(), n_pairs)
     P = pos[torch.randint(0, pos.numel(), (npos,), device="cuda", generator=g)]
