@@ -174,9 +174,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // S = sum (a_c - b_c)^2 of two rows held in shared memory as nch 16-byte
-// chunks (nch even).  A lane starts at chunk `rot` mod nch and wraps around,
+// chunks (nch even).  Each step takes chunk q and its partner q + nch/2; a
+// lane starts at q = rot mod nch/2 and wraps around within the first half,
 // so the 8 lanes of a quarter warp read 8 different chunks (32 different
-// banks) whatever rows they hold.  Eight fma chains over at most dim / 8
+// banks) whatever rows they hold, all lanes in step.  Eight fma chains over at most dim / 8
 // coordinates each: with the difference's rounding (2u in its square) and
 // three levels combining the chains, |S' - S| <= (dim / 8 + 8) u S.
 __device__ __forceinline__ float smem_sq_dist(const unsigned char* a, const unsigned char* b,
@@ -186,10 +187,10 @@ __device__ __forceinline__ float smem_sq_dist(const unsigned char* a, const unsi
   float c[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) c[m] = 0.f;
-  int q = rot % nch;
-  for (int t = 0; t < nch; t += 2) {
-    const int q1 = q + 1 == nch ? 0 : q + 1;
-    const uint4 x0 = a4[q], y0 = b4[q], x1 = a4[q1], y1 = b4[q1];
+  const int h = nch / 2;
+  int q = rot % h;
+  for (int t = 0; t < h; ++t) {
+    const uint4 x0 = a4[q], y0 = b4[q], x1 = a4[q + h], y1 = b4[q + h];
     if (dtype == MSM_DT_BF16) {  // 8 values per chunk: value v of a chunk feeds chain v
       const uint32_t xa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
       const uint32_t ya[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
@@ -200,7 +201,7 @@ __device__ __forceinline__ float smem_sq_dist(const unsigned char* a, const unsi
         c[(2 * w) & 7] = fmaf(t0, t0, c[(2 * w) & 7]);
         c[(2 * w + 1) & 7] = fmaf(t1, t1, c[(2 * w + 1) & 7]);
       }
-    } else {  // 4 floats per chunk: the first chunk feeds chains 0-3, the second 4-7
+    } else {  // 4 floats per chunk: chunk q feeds chains 0-3, its partner 4-7
       const float d0 = __uint_as_float(x0.x) - __uint_as_float(y0.x);
       const float d1 = __uint_as_float(x0.y) - __uint_as_float(y0.y);
       const float d2 = __uint_as_float(x0.z) - __uint_as_float(y0.z);
@@ -218,7 +219,7 @@ __device__ __forceinline__ float smem_sq_dist(const unsigned char* a, const unsi
       c[6] = fmaf(d6, d6, c[6]);
       c[7] = fmaf(d7, d7, c[7]);
     }
-    q = q1 + 1 == nch ? 0 : q1 + 1;
+    q = q + 1 == h ? 0 : q + 1;
   }
   return ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
 }
