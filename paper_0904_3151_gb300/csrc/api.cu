@@ -341,7 +341,6 @@ static int check_sets(const int64_t* off, int S, int64_t* n) {
   return MSM_OK;
 }
 
-// Count-only recheck fused into the pair check (X == NULL: not fused).
 // Dense-tile records of a pair-list run (run_msm with recs_out): the
 // records themselves and how many there are, and the pairs they hold.
 struct RecsOut {
@@ -350,6 +349,7 @@ struct RecsOut {
   int64_t pairs = 0;
 };
 
+// Count-only recheck fused into the pair check (X == NULL: not fused).
 struct FuseCfg {
   const void* X = nullptr;
   int dtype = 0, dim = 0, metric = 0;
@@ -492,80 +492,80 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
   // keeps the host off the GPU's path (and copies of earlier results on
   // other streams from delaying it).
   for (;;) {
-  for (int q = 0; q < Q; ++q) {
-    const uint64_t* pool = strings + (size_t)q * n * W;
-    for (int m0 = 0; m0 < M; m0 += (int)Sb) {
-      const int S = (int)((M - m0) < Sb ? (M - m0) : Sb);
-      GroupBatch gbt;
-      gbt.strings = pool;
-      gbt.n = n;
-      gbt.W = W;
-      gbt.masks = dM + m0;
-      gbt.S = S;
-      gbt.group_bits = gb;
-      gbt.passes = passes;
-      gbt.layout = dL;
-      gbt.sets = sets;
-      uint32_t *keys = nullptr, *vals = nullptr;
-      tm.mark(2);
-      int rc = run_grouping(gbt, gws, &keys, &vals, s);
-      if (rc) return rc;
-      PairBatch pb;
-      pb.keys = keys;
-      pb.vals = vals;
-      pb.strings = strings;
-      pb.n = n;
-      pb.W = W;
-      pb.S = S;
-      pb.q = q;
-      pb.d = d;
-      pb.group_bits = gb;
-      pb.masks = dM + m0;
-      pb.layout = dL;
-      pb.fields = fields;
-      pb.FP = FP;
-      pb.FU = (k + 1) / 2;
-      pb.sw = sw;
-      pb.start_bits = sets.start_bits;
-      pb.X = fz.X;
-      pb.dtype = fz.dtype;
-      pb.dim = fz.dim;
-      pb.metric = fz.metric;
-      pb.eps = fz.eps;
-      pb.nrm = fz.nrm;
-      pb.kept = fz.kept;
-      pb.set_kept = fz.set_kept;
-      pb.set_off = sets.off;
-      pb.nsets = sets.S;
-      pb.evaluated = eval_dev;
-      pb.ctas_per_sm = tu.check_ctas_per_sm;
-      pb.min_blocks = tu.check_min_blocks;
-      pb.recs = recs;
-      tm.mark(3);
-      rc = find_groups(pb, pws, checks_dev, s);
-      if (rc) return rc;
-      tm.mark(4);
-      rc = check_groups(pb, pws, fused ? nullptr : cand, fused ? 0 : cap, count_dev, s);
-      if (rc) return rc;
+    for (int q = 0; q < Q; ++q) {
+      const uint64_t* pool = strings + (size_t)q * n * W;
+      for (int m0 = 0; m0 < M; m0 += (int)Sb) {
+        const int S = (int)((M - m0) < Sb ? (M - m0) : Sb);
+        GroupBatch gbt;
+        gbt.strings = pool;
+        gbt.n = n;
+        gbt.W = W;
+        gbt.masks = dM + m0;
+        gbt.S = S;
+        gbt.group_bits = gb;
+        gbt.passes = passes;
+        gbt.layout = dL;
+        gbt.sets = sets;
+        uint32_t *keys = nullptr, *vals = nullptr;
+        tm.mark(2);
+        int rc = run_grouping(gbt, gws, &keys, &vals, s);
+        if (rc) return rc;
+        PairBatch pb;
+        pb.keys = keys;
+        pb.vals = vals;
+        pb.strings = strings;
+        pb.n = n;
+        pb.W = W;
+        pb.S = S;
+        pb.q = q;
+        pb.d = d;
+        pb.group_bits = gb;
+        pb.masks = dM + m0;
+        pb.layout = dL;
+        pb.fields = fields;
+        pb.FP = FP;
+        pb.FU = (k + 1) / 2;
+        pb.sw = sw;
+        pb.start_bits = sets.start_bits;
+        pb.X = fz.X;
+        pb.dtype = fz.dtype;
+        pb.dim = fz.dim;
+        pb.metric = fz.metric;
+        pb.eps = fz.eps;
+        pb.nrm = fz.nrm;
+        pb.kept = fz.kept;
+        pb.set_kept = fz.set_kept;
+        pb.set_off = sets.off;
+        pb.nsets = sets.S;
+        pb.evaluated = eval_dev;
+        pb.ctas_per_sm = tu.check_ctas_per_sm;
+        pb.min_blocks = tu.check_min_blocks;
+        pb.recs = recs;
+        tm.mark(3);
+        rc = find_groups(pb, pws, checks_dev, s);
+        if (rc) return rc;
+        tm.mark(4);
+        rc = check_groups(pb, pws, fused ? nullptr : cand, fused ? 0 : cap, count_dev, s);
+        if (rc) return rc;
+      }
     }
-  }
-  tm.mark(-1);
-  if (fused) break;  // candidates were rechecked and counted in place
-  unsigned long long c = 0;
-  int rc = read_back(&c, count_dev, s);
-  if (rc) return rc;
-  if ((int64_t)c <= cap) {
-    count = (int64_t)c;
-    break;
-  }
-  // E was too small: grow it to the final count and enumerate again.
-  int64_t ncap = (int64_t)c + (int64_t)c / 8 + 1024;
-  sc.put(cand);
-  cand = (uint64_t*)sc.get(8 * (size_t)ncap);
-  if (!cand) return MSM_E_NOMEM;
-  cap = ncap;
-  MSM_CUDA(cudaMemsetAsync(counters, 0, 256, s));
-  ++retries;
+    tm.mark(-1);
+    if (fused) break;  // candidates were rechecked and counted in place
+    unsigned long long c = 0;
+    int rc = read_back(&c, count_dev, s);
+    if (rc) return rc;
+    if ((int64_t)c <= cap) {
+      count = (int64_t)c;
+      break;
+    }
+    // E was too small: grow it to the final count and enumerate again.
+    int64_t ncap = (int64_t)c + (int64_t)c / 8 + 1024;
+    sc.put(cand);
+    cand = (uint64_t*)sc.get(8 * (size_t)ncap);
+    if (!cand) return MSM_E_NOMEM;
+    cap = ncap;
+    MSM_CUDA(cudaMemsetAsync(counters, 0, 256, s));
+    ++retries;
   }
   total_cand = count;
   if (recs.pool) {
