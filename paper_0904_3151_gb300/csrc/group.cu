@@ -242,7 +242,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v,
 }
 
 template <typename KeyT, bool FROM_STR, int IPT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 scatter_kernel(SortArgs a) {
   constexpr int TILE = kThreads * IPT;
   constexpr int PER_WARP = 32 * IPT;
@@ -283,15 +283,24 @@ scatter_kernel(SortArgs a) {
     bool valid = e < cnt;
     const KeyT k = key[r];
     const uint32_t v = val[r];
+    (void)v;
     uint32_t digit = valid ? ((uint32_t)(k >> a.shift) & 0xFFu) : 0xFFFFFFFFu;
-    unsigned peers = __match_any_sync(0xffffffffu, digit);
-    int leader = __ffs(peers) - 1;
-    uint32_t old = 0;
-    if (valid && lane == leader) old = wh[warp][digit];
-    old = __shfl_sync(0xffffffffu, old, leader);
-    if (valid && lane == leader) wh[warp][digit] = old + __popc(peers);
-    __syncwarp();
-    rank[r] = old + __popc(peers & lt_mask);
+    if constexpr (FROM_STR) {
+      // The first pass reads the items in point order, which nothing below
+      // depends on (an LSD sort needs stable passes only after its first;
+      // the one-set grouping only needs equal keys together), so an item's
+      // rank within its warp and digit is the order of a shared atomic.
+      rank[r] = valid ? atomicAdd(&wh[warp][digit], 1u) : 0u;
+    } else {
+      unsigned peers = __match_any_sync(0xffffffffu, digit);
+      int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (valid && lane == leader) old = wh[warp][digit];
+      old = __shfl_sync(0xffffffffu, old, leader);
+      if (valid && lane == leader) wh[warp][digit] = old + __popc(peers);
+      __syncwarp();
+      rank[r] = old + __popc(peers & lt_mask);
+    }
   }
   __syncthreads();
   // Per digit: prefix over warps, tile total, and the tile's digit start.
