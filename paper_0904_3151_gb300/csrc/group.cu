@@ -374,10 +374,13 @@ __device__ __forceinline__ int per_warp_items(int m) {
 // Stable rank of the digit (key >> shift) & 0xFF of the first m items
 // (held as above, pw items per warp): pos[r] gets the item's place in the
 // digit-sorted order, sm.dstart the digit starts and sm.wh[w][d] the count
-// of digit d in warps before w.  Ends synchronised.
+// of digit d in warps before w.  Ends synchronised.  Not `stable` (the first
+// of the LSD passes, whose input order nothing depends on): the rank within a
+// warp and digit is the order of a shared atomic instead of the item order.
 template <int IPT>
 __device__ __forceinline__ void bucket_rank(const uint32_t (&key)[IPT], int shift, int m,
-                                            int pw, uint32_t (&pos)[IPT], BucketSmem& sm) {
+                                            int pw, uint32_t (&pos)[IPT], BucketSmem& sm,
+                                            bool stable) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int rounds = pw / 32;
@@ -389,6 +392,10 @@ __device__ __forceinline__ void bucket_rank(const uint32_t (&key)[IPT], int shif
     const int e = warp * pw + r * 32 + lane;
     const bool valid = e < m;
     const uint32_t digit = valid ? (key[r] >> shift) & 0xFFu : 0xFFFFFFFFu;
+    if (!stable) {  // warp-uniform
+      pos[r] = valid ? atomicAdd(&sm.wh[warp][digit], 1u) : 0u;
+      continue;
+    }
     const unsigned peers = __match_any_sync(0xffffffffu, digit);
     const int leader = __ffs(peers) - 1;
     uint32_t old = 0;
@@ -450,7 +457,7 @@ bucket_sort_kernel(BucketArgs a) {
       }
     }
     for (int p = 0; p < a.passes; ++p) {
-      bucket_rank<kBIpt>(key, 8 * p, (int)m, pw, pos, sm);
+      bucket_rank<kBIpt>(key, 8 * p, (int)m, pw, pos, sm, p > 0);
 #pragma unroll
       for (int r = 0; r < kBIpt; ++r) {
         if (r >= rounds) break;
@@ -507,7 +514,7 @@ bucket_sort_kernel(BucketArgs a) {
           val[r] = sv[c0 + e];
         }
       }
-      bucket_rank<kBIpt>(key, shift, cm, pw, pos, sm);
+      bucket_rank<kBIpt>(key, shift, cm, pw, pos, sm, p > 0);
 #pragma unroll
       for (int r = 0; r < kBIpt; ++r) {
         if (r >= rounds) break;
