@@ -6,7 +6,7 @@
 // never stored unsorted.
 //
 // One point set: a most-significant-digit pass (shared-memory histograms,
-// one exclusive scan, stable scatter with warp-level ranking) splits every
+// one exclusive scan, scatter ranked by shared atomics) splits every
 // segment into 256 buckets by the top 8 key bits, then one CTA per bucket
 // sorts it by the remaining bits in shared memory (three 8-bit LSD passes
 // between registers and shared memory) and writes it back in place: one
@@ -430,7 +430,8 @@ __device__ __forceinline__ void bucket_rank(const uint32_t (&key)[IPT], int shif
 }
 
 // One CTA per (segment, top digit) bucket: sort its items by the bits below
-// the top digit (stable, so equal keys keep their point order).
+// the top digit (the last two passes stable; equal keys end up together in
+// no particular order).
 __global__ void __launch_bounds__(kBT, 2)
 bucket_sort_kernel(BucketArgs a) {
   extern __shared__ __align__(16) unsigned char bucket_smem[];
