@@ -871,22 +871,22 @@ def main():
     # followed by the device->host read of its pairs and distances into
     # pinned host buffers.  The read of step r runs on a second stream while
     # step r + 1 computes (two host buffer pairs, alternating), as a stream
-    # of jobs would run; the timed region ends when the last read lands.
+    # of jobs would run; the warm-up steps run the same pattern, and the
+    # timed region (K steps) ends when the last read lands.
     e2e = None
     if not a.no_e2e:
         Xpin = torch.from_numpy(Xh).pin_memory()
-        reps = max(2, min(3, a.steps))
-        p, dv, st = step(Xpin)          # warm
+        reps = max(3, a.steps)
+        p, dv, st = step(Xpin)          # sizes the host buffers
         cap = p.numel()  # the same input gives the same pairs every step
         host = [(torch.empty(cap, dtype=torch.int64, pin_memory=True),
                  torch.empty(cap, dtype=torch.float32, pin_memory=True)) for _ in range(2)]
         del p, dv
         side = torch.cuda.Stream()
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        bo = 0
-        for r in range(reps):
+        ch = a.e2e_chunk if a.e2e_chunk > 0 else None
+
+        def e2e_step(r):
+            nonlocal cap, host
             p, dv, st = step(Xpin)
             m = p.numel()
             if m > cap:  # not expected: the same input gives the same count
@@ -899,23 +899,32 @@ def main():
             ready.record(stream)
             side.wait_event(ready)
             hp, hd = host[r % 2]
-            ch = a.e2e_chunk if a.e2e_chunk > 0 else max(1, m)
+            step_ch = ch or max(1, m)
             with torch.cuda.stream(side):
-                for c0 in range(0, m, ch):
-                    c1 = min(m, c0 + ch)
+                for c0 in range(0, m, step_ch):
+                    c1 = min(m, c0 + step_ch)
                     hp[c0:c1].copy_(p[c0:c1], non_blocking=True)
                     hd[c0:c1].copy_(dv[c0:c1], non_blocking=True)
             p.record_stream(side)
             dv.record_stream(side)
-            bo = m * 8 + dv.numel() * 4
-            del p, dv
+            return m * 8 + dv.numel() * 4
+
+        for r in range(max(3, a.warmup)):
+            e2e_step(r)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        bo = 0
+        for r in range(reps):
+            bo = e2e_step(r)
         stream.wait_stream(side)
         f1.record(stream)
         torch.cuda.synchronize()
         ems = replicas.max_over_ranks(f0.elapsed_time(f1) / reps, dist, "cuda")
         e2e = {"value": replicas.job_throughput(world, n, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(Xh.nbytes), "d2h_bytes_per_step": int(bo),
-               "ms_per_step": ems, "steps": reps,
+               "ms_per_step": ems, "steps": reps, "warmup": max(3, a.warmup),
                "overlap": "device->host read of step r on a second stream during step r+1, "
                           f"in copies of {a.e2e_chunk} pairs"}
 
