@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "msm_internal.cuh"
+#include "readback.cuh"
 
 namespace msm {
 
@@ -98,6 +99,39 @@ int num_sms() {
     cache[dev] = v;
   }
   return cache[dev];
+}
+
+// ------------------------------------------------------- small read-backs
+__global__ void read_words_kernel(const uint32_t* src, uint32_t* dst, int nwords) {
+  for (int i = threadIdx.x; i < nwords; i += blockDim.x) dst[i] = src[i];
+  __threadfence_system();
+}
+
+int read_to_host(void* host, const void* dev, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return MSM_OK;
+  if (bytes % 4 || bytes > kReadBackBytes || ((uintptr_t)dev & 3))
+    return set_error("read-back of %zu bytes: not whole aligned words within %zu", bytes,
+                     kReadBackBytes), MSM_E_INVAL;
+  // One buffer per host thread (a call reads back only between its own
+  // launches and waits for the read), kept for the life of the process; it is
+  // allocated again if its context has gone (a device reset).
+  static thread_local uint32_t* mapped = nullptr;
+  uint32_t* dptr = nullptr;
+  if (mapped && cudaHostGetDevicePointer((void**)&dptr, mapped, 0) != cudaSuccess) {
+    cudaGetLastError();
+    mapped = nullptr;
+  }
+  if (!mapped) {
+    void* p = nullptr;
+    MSM_CUDA(cudaHostAlloc(&p, kReadBackBytes, cudaHostAllocMapped | cudaHostAllocPortable));
+    mapped = (uint32_t*)p;
+    MSM_CUDA(cudaHostGetDevicePointer((void**)&dptr, mapped, 0));
+  }
+  read_words_kernel<<<1, 32, 0, s>>>((const uint32_t*)dev, dptr, (int)(bytes / 4));
+  MSM_LAUNCH("read_words_kernel");
+  MSM_CUDA(cudaStreamSynchronize(s));
+  std::memcpy(host, mapped, bytes);
+  return MSM_OK;
 }
 
 // ------------------------------------------------------------------ memory
@@ -287,9 +321,8 @@ struct PhaseTimer {
 
 template <typename T>
 static int read_back(T* host, const T* dev, cudaStream_t s) {
-  MSM_CUDA(cudaMemcpyAsync(host, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
-  MSM_CUDA(cudaStreamSynchronize(s));
-  return MSM_OK;
+  static_assert(sizeof(T) % 4 == 0, "read-backs move whole 4-byte words");
+  return read_to_host(host, dev, sizeof(T), s);
 }
 
 // Device set table for the host offsets off[0..S] (validated by the caller:
@@ -570,8 +603,8 @@ static int run_msm(Scratch& sc, const uint64_t* strings, int64_t n, int ell, int
   total_cand = count;
   if (recs.pool) {
     unsigned long long h[3] = {0, 0, 0};
-    MSM_CUDA(cudaMemcpyAsync(h, recs.ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
-    MSM_CUDA(cudaStreamSynchronize(s));
+    int rc = read_to_host(h, recs.ctr, sizeof(h), s);
+    if (rc) return rc;
     recs_out->recs = recs;
     recs_out->nrec = (uint32_t)(h[0] < recs.cap ? h[0] : recs.cap);
     recs_out->pairs = (int64_t)h[2];
@@ -992,8 +1025,8 @@ int msm_recheck(const void* X, int64_t n, int dim, int dtype, int metric,
                       pairs_out, dist_out, ctr, ctr + 1, (unsigned*)(ctr + 2), s);
   if (rc) return rc;
   unsigned long long h[3] = {0, 0, 0};
-  MSM_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
-  MSM_CUDA(cudaStreamSynchronize(s));
+  rc = read_to_host(h, ctr, sizeof(h), s);
+  if (rc) return rc;
   if (h[2]) return set_error("a candidate is not a pair i < j < n"), MSM_E_INVAL;
   *count = (int64_t)h[0];
   if (recomputed) *recomputed = (int64_t)h[1];
@@ -1206,8 +1239,8 @@ static int eps_graph_impl(const void* X, int64_t n, const int64_t* off, int S, i
                             ctr, ctr + 1, s);
   if (rc) return rc;
   unsigned long long h[3] = {0, 0, 0};
-  MSM_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
-  MSM_CUDA(cudaStreamSynchronize(s));
+  rc = read_to_host(h, ctr, sizeof(h), s);
+  if (rc) return rc;
   const int64_t kept = (int64_t)h[0];
   sc.put(cand);
   if (ro.recs.pool) {

@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include "msm_internal.cuh"
+#include "readback.cuh"
 #include "tcgen05.cuh"
 
 namespace msm {
@@ -414,8 +415,8 @@ int launch_mlp_tc(const void* X, int dtype, int64_t n, int dim, const void* W1,
   kt_end(s);
   MSM_LAUNCH("mlp_tc_kernel");
   unsigned st = 0;
-  MSM_CUDA(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
-  MSM_CUDA(cudaStreamSynchronize(s));
+  rc = read_to_host(&st, status, 4, s);
+  if (rc) return rc;
   if (st & 1u) return set_error("tensor-core feature map: a bounded wait timed out"), MSM_E_TIMEOUT;
   return MSM_OK;
 }

@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 
 #include "msm_internal.cuh"
+#include "readback.cuh"
 #include "tcgen05.cuh"
 
 namespace msm {
@@ -586,10 +587,11 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
   // queued bits; an overflowing queue means the tensor-core pass cannot be
   // completed from it, so the caller reruns the projection on the SIMT path
   unsigned long long cnt = 0;
-  MSM_CUDA(cudaMemcpyAsync(&cnt, fix_count, 8, cudaMemcpyDeviceToHost, s));
-  MSM_CUDA(cudaStreamSynchronize(s));
+  rc = read_to_host(&cnt, fix_count, 8, s);
+  if (rc) return rc;
   unsigned st = 0;
-  MSM_CUDA(cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost));
+  rc = read_to_host(&st, status, 4, s);
+  if (rc) return rc;
   if (st & 1u) return set_error("tensor-core projection: a bounded wait timed out"), MSM_E_TIMEOUT;
   if ((int64_t)cnt > fix_cap) {
     *fell_back = true;
@@ -607,8 +609,8 @@ int launch_project_tc(const void* X, int dtype, int64_t n, int dim,
     kt_end(s);
     MSM_LAUNCH("project_fix_kernel");
     unsigned long long dcnt = 0;
-    MSM_CUDA(cudaMemcpyAsync(&dcnt, dq_count, 8, cudaMemcpyDeviceToHost, s));
-    MSM_CUDA(cudaStreamSynchronize(s));
+    rc = read_to_host(&dcnt, dq_count, 8, s);
+    if (rc) return rc;
     if ((int64_t)dcnt > dq_cap) {
       *fell_back = true;
       return MSM_OK;
