@@ -14,7 +14,11 @@
  *     the current device; "host" pointers are ordinary CPU memory.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Work is enqueued on it; calls that must read a count back
- *     (documented) synchronise on it before returning.
+ *     (documented) synchronise on it before returning.  Such reads go through
+ *     a 1 KB host-mapped pinned buffer per calling thread (allocated by its
+ *     first read, kept for the life of the process) written by a one-warp
+ *     kernel, not through a copy engine, so a device-to-host copy that the
+ *     caller keeps running on another stream does not hold them up.
  *   - Inputs are never modified.  Return value is MSM_OK or a negative
  *     MSM_E_* code; msm_last_error() gives a message for the calling thread.
  *   - Pair encoding: (uint64_t)i << 32 | j with 0 <= i < j < n.
